@@ -1,0 +1,214 @@
+/*
+ * gbfwi.h - C ABI of the GB300 (sm_103a) library for the data-parallel hot
+ * path of preconditioned-BFGS elastic full-waveform inversion with low-rank
+ * uncertainty quantification (Liu, Beller, Lei, Peter & Tromp 2020,
+ * "Preconditioned BFGS-based uncertainty quantification in elastic full
+ * waveform inversion").
+ *
+ * The path: forward and adjoint 2-D isotropic elastic spectral-element
+ * simulations (Section 3.1, Appendix A, Eqs. A6-A18) giving the misfit of
+ * Eq. A1 and its gradient; the diagonal Gauss-Newton / illumination maps
+ * P1-P4 (Eqs. 4-8, A21-A22) smoothed, damped and inverted into B0; the
+ * full-history BFGS inverse Hessian (Eqs. 3 and 9, Algorithms 1-2) applied in
+ * compact form to blocks of vectors; and the single-pass randomized SVD of
+ * Algorithm 3 giving the low-rank posterior covariance of Eqs. 10-14.
+ *
+ * Conventions (every entry point):
+ *   - Return value: GBFWI_OK (0) or a negative GBFWI_E* code; output
+ *     arguments are written only on success.  gbfwi_strerror() names a code.
+ *   - Arrays: the caller owns every array argument.  Each array may be host
+ *     or device memory; the library looks at the pointer (CUDA pointer
+ *     attributes).  Host arrays are staged through library-owned device
+ *     buffers and the call returns only after its host outputs are written;
+ *     with device arrays the work is queued on `stream` (a cudaStream_t, or
+ *     NULL for the legacy default stream) and the call returns once it is
+ *     queued, except where an entry point says it synchronises.
+ *   - Handles (gbfwi_mesh, gbfwi_bfgs) are opaque and library-owned; create
+ *     and destroy them through this ABI.  A handle is not thread-safe: use
+ *     one handle per host thread / stream.
+ *   - Layout: node-grid fields are row-major [nz][nx] with nx = 4 nex + 1,
+ *     nz = 4 nez + 1, row 0 at the surface and z = depth (GLL nodes of a
+ *     structured mesh of square elements, NGLL = 5).  Parameter vectors are
+ *     [3][nz][nx] in the order rho, vp, vs (n = 3 nx nz).  Seismograms are
+ *     [nshot][nrec][2][nt] (x then z displacement component), sample n-1
+ *     holding time step n (t = n dt), n = 1..nt.
+ *   - Precision: wavefields, models, kernels and BFGS vectors are FP32;
+ *     misfits and the small BFGS / randomized-SVD matrices are FP64.
+ */
+#ifndef GBFWI_H
+#define GBFWI_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GBFWI_OK = 0,
+    GBFWI_EINVAL = -1,      /* bad argument (size, pointer, range, order of calls) */
+    GBFWI_ENOMEM = -2,      /* device or host allocation failed */
+    GBFWI_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed */
+    GBFWI_ECFL = -4,        /* dt * vp_max / (min GLL node spacing) > 0.5 */
+    GBFWI_ECURV = -5,       /* BFGS pair rejected: y^T s <= 1e-12 |s| |y| */
+    GBFWI_ENONFINITE = -6,  /* a NaN or Inf reached the seismograms or the model */
+    GBFWI_ETIMEOUT = -7,    /* a bounded device-side wait gave up */
+    GBFWI_ENOMODEL = -8     /* simulation requested before gbfwi_set_model */
+};
+
+typedef struct gbfwi_mesh gbfwi_mesh;
+typedef struct gbfwi_bfgs gbfwi_bfgs;
+
+/* Structured quad mesh and time axis (Section 3.1: spectral elements,
+ * absorbing boundaries; the paper's runs use SPECFEM2D).  Edges other than
+ * the top are first-order Stacey absorbing boundaries. */
+typedef struct {
+    int nex, nez;           /* elements along x and along depth (>= 1) */
+    double h;               /* element side in metres (> 0) */
+    int ngll;               /* GLL points per direction: must be 5 */
+    int free_surface_top;   /* 1: traction-free top edge, 0: Stacey on top too */
+    double dt;              /* time step in seconds (> 0) */
+    int nt;                 /* time steps; records at n = 1..nt (>= 2) */
+    int precision;          /* 0 = FP32 wavefields (the only value accepted) */
+} gbfwi_mesh_desc;
+
+/* Ricker point source, r(t) = amp (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2)
+ * (Section 3.1 uses a Ricker wavelet).  type 0: explosive moment tensor
+ * amp * I (nodal force amp * grad psi(x_s)); type 1 / 2: point force along
+ * x / z (nodal force amp * psi(x_s)).  A point on a shared element edge
+ * belongs to the element of smaller index. */
+typedef struct {
+    double x, z;            /* position in metres, z = depth */
+    int type;               /* 0 explosive, 1 force x, 2 force z */
+    double f0, t0, amp;     /* peak frequency (Hz), delay (s), amplitude */
+} gbfwi_source;
+
+/* Launch schedule (chosen by the autotuner or the caller). */
+typedef struct {
+    int shots_per_launch;   /* shots advanced together in one launch (>= 1) */
+    int tile;               /* element-tile variant, 0..gbfwi_num_tiles()-1 */
+    int use_graph;          /* 1: replay the time loop as CUDA graphs */
+    int ckpt_every;         /* 0: keep the whole forward history on the device;
+                               k > 0: keep a snapshot every k steps and
+                               recompute each segment during the adjoint */
+} gbfwi_schedule;
+
+/* ---------------------------------------------------------------- mesh -- */
+
+/* Build the mesh, GLL tables, source and receiver interpolation tables.
+ * src[nsrc] (host), rec_xz[nrec][2] (host, x then depth).  Every point must
+ * lie inside the mesh.  -> EINVAL, ENOMEM, ECUDA.  *out receives the handle. */
+int gbfwi_mesh_create(const gbfwi_mesh_desc *desc, const gbfwi_source *src, int nsrc,
+                      const double *rec_xz, int nrec, gbfwi_mesh **out);
+
+/* Free the mesh and every device buffer it owns.  NULL is accepted. */
+int gbfwi_mesh_destroy(gbfwi_mesh *mesh);
+
+/* Node-grid size: *nx = 4 nex + 1, *nz = 4 nez + 1. */
+int gbfwi_mesh_dims(const gbfwi_mesh *mesh, int *nx, int *nz);
+
+/* Node coordinates in metres, host arrays [nz][nx]. */
+int gbfwi_node_coords(const gbfwi_mesh *mesh, double *x, double *z);
+
+/* Number of element-tile variants the library was built with, and their
+ * shapes (tile elements along x, along z). */
+int gbfwi_num_tiles(void);
+int gbfwi_tile_shape(int tile, int *tx, int *tz);
+
+/* Read / replace the launch schedule. */
+int gbfwi_get_schedule(const gbfwi_mesh *mesh, gbfwi_schedule *sch);
+int gbfwi_set_schedule(gbfwi_mesh *mesh, const gbfwi_schedule *sch);
+
+/* Model on the node grid, each [nz][nx] FP32 (Eq. A7 parametrisation
+ * alpha = vp, beta = vs, rho): lambda = rho (vp^2 - 2 vs^2), mu = rho vs^2.
+ * Checks rho > 0, vp > vs > 0, finite values, and the stability bound
+ * dt vp_max / dx_min <= 0.5 (dx_min = smallest GLL node spacing) -> ECFL.
+ * Synchronises the stream (the check reads the model on the host). */
+int gbfwi_set_model(gbfwi_mesh *mesh, const float *rho, const float *vp, const float *vs,
+                    void *stream);
+
+/* ------------------------------------------------------------ simulate -- */
+
+/* Forward simulations (Eqs. A6-A7, Newmark beta = 0, gamma = 1/2 with
+ * implicit Stacey damping) from rest for the sources shot_ids[nshot] (host
+ * ints indexing the mesh's sources).  seis: [nshot][nrec][2][nt] receiver
+ * displacements s_n = P u_n.  -> EINVAL, ENOMODEL, ECUDA, ENOMEM. */
+int gbfwi_forward(gbfwi_mesh *mesh, const int *shot_ids, int nshot, float *seis, void *stream);
+
+/* Misfit f = 1/2 dt sum |s - d|^2 (Eq. A1) and its exact discrete gradient
+ * with respect to the nodal (rho, vp, vs) (the discrete form of Eqs.
+ * A16-A18: the adjoint of the time stepping, run backwards and correlated
+ * with the forward field), summed over the shots.  d_obs: [nshot][nrec][2][nt]
+ * observed data in shot_ids order.  *misfit: host double.  grad: [3][nz][nx].
+ * ckpt_every < 0 keeps the mesh schedule; >= 0 overrides its ckpt_every.
+ * Synchronises the stream (the misfit is returned on the host).
+ * -> EINVAL, ENOMODEL, ENONFINITE, ECUDA, ENOMEM. */
+int gbfwi_adjoint_gradient(gbfwi_mesh *mesh, const int *shot_ids, int nshot,
+                           const float *d_obs, double *misfit, float *grad,
+                           int ckpt_every, void *stream);
+
+/* Diagonal Hessian preconditioner of kind 1..4 (Eqs. 4-8, A21-A22), summed
+ * over the shots: P1 source illumination int a.a dt, P2 |int a.abar dt|,
+ * P3 Gauss-Newton H_alpha_alpha / H_beta_beta of the source wavefield,
+ * P4 the same with the receiver wavefield (driven by the synthetic data,
+ * after Eq. A22) and term-wise absolute values.  Each map carries the
+ * quadrature measure of its node (like the gradient).  The rho entry is
+ * H_rho_rho (Eq. A21/A22, third line) for every kind; P1/P2 give the same
+ * map for rho, vp and vs.
+ * H:  [3][nz][nx] raw map (may be NULL).
+ * B0: [3][nz][nx] = 1 / (S(H) + damp_factor * median(S(H))) per parameter,
+ *     S = Gaussian smoothing of standard deviation smooth_sigma_m metres
+ *     (quadrature-weighted average in physical space, truncated at 5 sigma).
+ * Synchronises the stream.  -> EINVAL, ENOMODEL, ECUDA, ENOMEM. */
+int gbfwi_precond_diag(gbfwi_mesh *mesh, const int *shot_ids, int nshot, int kind,
+                       double smooth_sigma_m, double damp_factor, float *H, float *B0,
+                       void *stream);
+
+/* ---------------------------------------------------------------- BFGS -- */
+
+/* Full-history BFGS store for n unknowns and up to kmax pairs (Section 3.1:
+ * every s_i, y_i is kept; the paper memory-maps them), with the diagonal
+ * initial inverse Hessian B0[n] (Eq. 4; device or host, copied).  The
+ * store (2 kmax n FP32) lives on the current device.  -> EINVAL, ENOMEM. */
+int gbfwi_bfgs_create(long long n, int kmax, const float *B0, gbfwi_bfgs **out);
+
+/* Append the pair s = m_{k+1} - m_k, y = g_{k+1} - g_k (Eq. 2) and extend
+ * the small matrices S^T Y and Y^T B0 Y of the compact form.  A pair with
+ * y^T s <= 1e-12 |s| |y| is not stored -> ECURV; a full store -> EINVAL.
+ * Synchronises the stream (the curvature test is read on the host). */
+int gbfwi_bfgs_update(gbfwi_bfgs *b, const float *s, const float *y, void *stream);
+
+/* Pairs currently stored (>= 0), or a negative code. */
+int gbfwi_bfgs_count(const gbfwi_bfgs *b);
+
+/* Z = (H - minus_B0 * gamma B0) X for a block X[p][n] (rows are vectors),
+ * H the BFGS inverse Hessian of Eq. 3 started from gamma * B0 after all
+ * stored pairs (Eq. 9), applied in the compact form of Byrd, Nocedal &
+ * Schnabel (1994), which equals the two-loop recursions of Algorithms 1
+ * (gamma = gamma_k) and 2 (gamma = 1, minus_B0 = 1).  Z: [p][n].
+ * 1 <= p <= 256.  -> EINVAL, ECUDA, ENOMEM. */
+int gbfwi_bfgs_apply(gbfwi_bfgs *b, const float *X, int p, float *Z, double gamma,
+                     int minus_B0, void *stream);
+
+/* Low-rank inverse Hessian and posterior standard deviation (Algorithm 3
+ * on B_{n+1} - B0, Eqs. 10-14 with C_m = eps_prior I):
+ *   E = (B_{n+1} - B0) X, QR = E, Omega (Q^T X) = Q^T E (Omega symmetrised),
+ *   U Lambda U^T = Omega, V = Q U, eigenpairs ordered by |lambda| descending;
+ *   std_i = sqrt(eps_prior * max(0, sum_k V_ki^2 lambda_k + B0_i)).
+ * X: [p][n] probing block, or NULL to draw standard normals on the device
+ * from Philox4x32-10 with `seed` (counter = element index / 4).  V: [rank][n]
+ * (may be NULL), lambda: [rank] FP64 (may be NULL), std: [n] (may be NULL).
+ * 1 <= rank <= p <= 256.  Synchronises the stream.
+ * -> EINVAL, ECUDA, ENOMEM, ENONFINITE (a singular Q^T X or Gram matrix). */
+int gbfwi_lowrank_invhess(gbfwi_bfgs *b, const float *X, int p, int rank,
+                          unsigned long long seed, double eps_prior, float *V,
+                          double *lambda, float *std, void *stream);
+
+/* Free the store.  NULL is accepted. */
+int gbfwi_bfgs_destroy(gbfwi_bfgs *b);
+
+/* Static description of an error code. */
+const char *gbfwi_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBFWI_H */

@@ -14,8 +14,10 @@ ten rounds, the key bumped by (W0, W1) between rounds.
 Gaussian block X[p][n]: element i = row * n + col uses counter
 (i // 4 low 32 bits, i // 4 high 32 bits, 0, 0) and key (seed low, seed high);
 of the four words x0..x3, element i takes Box-Muller pair (x0, x1) when
-i % 4 < 2 and (x2, x3) otherwise, with u1 = (a + 1) / 2^32, u2 = b / 2^32,
-cos for the even member and sin for the odd one.
+i % 4 < 2 and (x2, x3) otherwise, with the 24-bit uniforms
+u1 = ((a >> 8) + 1) / 2^24 in (0, 1] and u2 = (b >> 8) / 2^24 in [0, 1)
+(exact in single and double precision), z = sqrt(-2 ln u1) * cos(2 pi u2)
+for the even member and * sin(2 pi u2) for the odd one.
 """
 from __future__ import annotations
 
@@ -58,10 +60,10 @@ def gaussian_block(seed: int, p: int, n: int) -> np.ndarray:
     w = philox4x32_10(ctr, key)
     lane = (i % np.uint64(4)).astype(np.int64)
     pair = lane // 2
-    a = np.where(pair == 0, w[:, 0], w[:, 2]).astype(np.float64)
-    b = np.where(pair == 0, w[:, 1], w[:, 3]).astype(np.float64)
-    u1 = (a + 1.0) / 4294967296.0
-    u2 = b / 4294967296.0
+    a = np.where(pair == 0, w[:, 0], w[:, 2]) >> np.uint64(8)
+    b = np.where(pair == 0, w[:, 1], w[:, 3]) >> np.uint64(8)
+    u1 = (a.astype(np.float64) + 1.0) / 16777216.0
+    u2 = b.astype(np.float64) / 16777216.0
     rad = np.sqrt(-2.0 * np.log(u1))
     ang = 2.0 * np.pi * u2
     z = np.where(lane % 2 == 0, rad * np.cos(ang), rad * np.sin(ang))

@@ -1,0 +1,191 @@
+"""GB300 (sm_103a) preconditioned-BFGS elastic FWI with low-rank uncertainty
+quantification (Liu, Beller, Lei, Peter & Tromp 2020).
+
+Python face of the C ABI in ``include/gbfwi.h``.  The entry points keep the
+ABI's names:
+
+    mesh_create, set_model, forward, adjoint_gradient, precond_diag,
+    bfgs_create, bfgs_update, bfgs_apply, lowrank_invhess
+
+and two small handle classes (:class:`Mesh`, :class:`Bfgs`) carry them as
+methods.  Every step of the computation runs in the CUDA library; this module
+only marshals arguments.  Arrays may be torch tensors (CUDA or host) or numpy
+arrays; outputs are written in place.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._lib import (ABI_SYMBOLS, GbfwiError, MeshDesc, Schedule, Source, check, lib, ptr,
+                   stream_of)
+
+__all__ = [
+    "Mesh", "Bfgs", "GbfwiError", "ABI_SYMBOLS", "mesh_create", "set_model", "forward",
+    "adjoint_gradient", "precond_diag", "bfgs_create", "bfgs_update", "bfgs_apply",
+    "lowrank_invhess", "num_tiles", "tile_shape", "lib",
+]
+
+F32, F64, I32 = np.float32, np.float64, np.int32
+
+
+def num_tiles() -> int:
+    return lib().gbfwi_num_tiles()
+
+
+def tile_shape(tile: int):
+    tx, tz = ctypes.c_int(), ctypes.c_int()
+    check(lib().gbfwi_tile_shape(tile, ctypes.byref(tx), ctypes.byref(tz)), "tile_shape")
+    return tx.value, tz.value
+
+
+class Mesh:
+    """Handle of a structured spectral-element mesh with its sources and
+    receivers (gbfwi_mesh)."""
+
+    def __init__(self, nex, nez, h, dt, nt, sources, rec_xz, free_surface_top=1):
+        d = MeshDesc(int(nex), int(nez), float(h), 5, int(free_surface_top), float(dt), int(nt), 0)
+        srcs = (Source * max(1, len(sources)))()
+        for i, s in enumerate(sources):
+            srcs[i] = Source(float(s["x"]), float(s["z"]), int(s.get("type", 0)), float(s["f0"]),
+                             float(s.get("t0", 1.2 / s["f0"])), float(s.get("amp", 1.0)))
+        rec = np.ascontiguousarray(np.asarray(rec_xz, dtype=np.float64).reshape(-1, 2))
+        h_ = ctypes.c_void_p()
+        check(lib().gbfwi_mesh_create(ctypes.byref(d), srcs, len(sources),
+                                      ctypes.c_void_p(rec.ctypes.data), len(rec), ctypes.byref(h_)),
+              "mesh_create")
+        self._h = h_
+        self.nex, self.nez, self.h, self.dt, self.nt = int(nex), int(nez), float(h), float(dt), int(nt)
+        self.nsrc, self.nrec = len(sources), len(rec)
+        nx, nz = ctypes.c_int(), ctypes.c_int()
+        check(lib().gbfwi_mesh_dims(self._h, ctypes.byref(nx), ctypes.byref(nz)), "mesh_dims")
+        self.nx, self.nz = nx.value, nz.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                lib().gbfwi_mesh_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    @property
+    def nglob(self) -> int:
+        return self.nx * self.nz
+
+    def node_coords(self):
+        x = np.zeros(self.nglob)
+        z = np.zeros(self.nglob)
+        check(lib().gbfwi_node_coords(self._h, ptr(x, F64), ptr(z, F64)), "node_coords")
+        return x.reshape(self.nz, self.nx), z.reshape(self.nz, self.nx)
+
+    @property
+    def schedule(self) -> dict:
+        s = Schedule()
+        check(lib().gbfwi_get_schedule(self._h, ctypes.byref(s)), "get_schedule")
+        return dict(shots_per_launch=s.shots_per_launch, tile=s.tile, use_graph=s.use_graph,
+                    ckpt_every=s.ckpt_every)
+
+    def set_schedule(self, shots_per_launch=1, tile=0, use_graph=0, ckpt_every=0):
+        s = Schedule(int(shots_per_launch), int(tile), int(use_graph), int(ckpt_every))
+        check(lib().gbfwi_set_schedule(self._h, ctypes.byref(s)), "set_schedule")
+
+    def set_model(self, rho, vp, vs):
+        check(lib().gbfwi_set_model(self._h, ptr(rho, F32), ptr(vp, F32), ptr(vs, F32),
+                                    stream_of(rho, vp, vs)), "set_model")
+
+    def forward(self, shot_ids, seis):
+        ids = np.ascontiguousarray(np.asarray(shot_ids, dtype=np.int32))
+        check(lib().gbfwi_forward(self._h, ptr(ids, I32), len(ids), ptr(seis, F32), stream_of(seis)),
+              "forward")
+        return seis
+
+    def adjoint_gradient(self, shot_ids, d_obs, grad, ckpt_every=-1) -> float:
+        ids = np.ascontiguousarray(np.asarray(shot_ids, dtype=np.int32))
+        mis = ctypes.c_double()
+        check(lib().gbfwi_adjoint_gradient(self._h, ptr(ids, I32), len(ids), ptr(d_obs, F32),
+                                           ctypes.byref(mis), ptr(grad, F32), int(ckpt_every),
+                                           stream_of(d_obs, grad)), "adjoint_gradient")
+        return mis.value
+
+    def precond_diag(self, shot_ids, kind, sigma, damp, H, B0):
+        ids = np.ascontiguousarray(np.asarray(shot_ids, dtype=np.int32))
+        check(lib().gbfwi_precond_diag(self._h, ptr(ids, I32), len(ids), int(kind), float(sigma),
+                                       float(damp), ptr(H, F32), ptr(B0, F32), stream_of(H, B0)),
+              "precond_diag")
+
+
+class Bfgs:
+    """Handle of a full-history BFGS store (gbfwi_bfgs)."""
+
+    def __init__(self, n, kmax, B0):
+        h_ = ctypes.c_void_p()
+        check(lib().gbfwi_bfgs_create(int(n), int(kmax), ptr(B0, F32), ctypes.byref(h_)), "bfgs_create")
+        self._h = h_
+        self.n, self.kmax = int(n), int(kmax)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                lib().gbfwi_bfgs_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    @property
+    def count(self) -> int:
+        return check(lib().gbfwi_bfgs_count(self._h), "bfgs_count")
+
+    def update(self, s, y):
+        check(lib().gbfwi_bfgs_update(self._h, ptr(s, F32), ptr(y, F32), stream_of(s, y)), "bfgs_update")
+
+    def apply(self, X, Z, gamma=1.0, minus_B0=False):
+        p = X.shape[0] if X.ndim == 2 else 1
+        check(lib().gbfwi_bfgs_apply(self._h, ptr(X, F32), p, ptr(Z, F32), float(gamma), int(bool(minus_B0)),
+                                     stream_of(X, Z)), "bfgs_apply")
+        return Z
+
+    def lowrank_invhess(self, p, rank, seed=0, eps_prior=1.0, X=None, V=None, lam=None, std=None):
+        check(lib().gbfwi_lowrank_invhess(self._h, ptr(X, F32), int(p), int(rank), int(seed),
+                                          float(eps_prior), ptr(V, F32), ptr(lam, F64), ptr(std, F32),
+                                          stream_of(X, V, lam, std)), "lowrank_invhess")
+
+
+# function-style names of the C ABI
+def mesh_create(*a, **k) -> Mesh:
+    return Mesh(*a, **k)
+
+
+def set_model(mesh: Mesh, rho, vp, vs):
+    return mesh.set_model(rho, vp, vs)
+
+
+def forward(mesh: Mesh, shot_ids, seis):
+    return mesh.forward(shot_ids, seis)
+
+
+def adjoint_gradient(mesh: Mesh, shot_ids, d_obs, grad, ckpt_every=-1):
+    return mesh.adjoint_gradient(shot_ids, d_obs, grad, ckpt_every)
+
+
+def precond_diag(mesh: Mesh, shot_ids, kind, sigma, damp, H, B0):
+    return mesh.precond_diag(shot_ids, kind, sigma, damp, H, B0)
+
+
+def bfgs_create(n, kmax, B0) -> Bfgs:
+    return Bfgs(n, kmax, B0)
+
+
+def bfgs_update(b: Bfgs, s, y):
+    return b.update(s, y)
+
+
+def bfgs_apply(b: Bfgs, X, Z, gamma=1.0, minus_B0=False):
+    return b.apply(X, Z, gamma, minus_B0)
+
+
+def lowrank_invhess(b: Bfgs, p, rank, seed=0, eps_prior=1.0, X=None, V=None, lam=None, std=None):
+    return b.lowrank_invhess(p, rank, seed, eps_prior, X, V, lam, std)

@@ -1,0 +1,722 @@
+// Full-history BFGS store, compact-form inverse-Hessian apply and the
+// single-pass randomized SVD of the posterior covariance (sm_103a).
+//
+// Paper: Section 2.1 (Eqs. 1-3, Algorithm 1), Section 2.3 (Eq. 9,
+// Algorithms 2-3, Eqs. 10-14).  The inverse Hessian after k pairs started
+// from H0 = gamma B0 is applied in the compact form of Byrd, Nocedal &
+// Schnabel (1994):
+//   H = H0 + [S  H0 Y] [[R^-T (D + Y^T H0 Y) R^-1, -R^-T], [-R^-1, 0]] [S^T; Y^T H0]
+// with R_ij = s_i^T y_j (i <= j), D = diag(s_i^T y_i).  It equals the
+// recursion of Eq. 3 and the two-loop recursions of Algorithms 1-2.
+//
+// Layout: vectors are rows, S / Y / B0Y are [kmax][n] FP32, blocks X / E / Q /
+// V are [p][n] FP32.  The n-long work is (a) split-K products A B^T with a
+// deterministic FP64 reduction over the splits and (b) row combinations
+// out = coef * rows; the small matrices (middle matrix, Cholesky factors,
+// Omega and its eigendecomposition) are FP64 and solved in one CTA.
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "gbfwi_internal.h"
+
+struct gbfwi_bfgs {
+    long long n = 0;
+    int kmax = 0, k = 0;
+    DevBuf S, Y, BY, B0;       // [kmax][n] x 3, [n]
+    std::vector<double> SY;    // [kmax][kmax]: SY[i*kmax + j] = s_i^T y_j (i <= j)
+    std::vector<double> YBY;   // [kmax][kmax]: y_i^T B0 y_j
+    DevBuf dSY, dYBY;          // device copies
+    DevBuf part;               // split-K partials
+    DevBuf small;              // FP64 small matrices
+    DevBuf coef;               // FP32 combination coefficients
+    DevBuf X, E, Q, V;         // [p][n] blocks
+    DevBuf stage;              // host staging
+    DevBuf flag;
+};
+
+namespace {
+
+constexpr int AT = 64;          // output tile of the split-K product
+constexpr int KI = 32;          // i-chunk staged per step
+
+// part[sx][a][b] = sum_{i in split sx} A[a][i] * w[i] * Bm[b][i]
+__global__ void __launch_bounds__(256) atb_partial(const float *__restrict__ A, long long lda, int ka,
+                                                   const float *__restrict__ Bm, long long ldb, int kb,
+                                                   const float *__restrict__ w, long long n, long long chunk,
+                                                   double *__restrict__ part)
+{
+    __shared__ float As[KI][AT + 1];
+    __shared__ float Bs[KI][AT + 1];
+    const int sx = blockIdx.x, a0 = blockIdx.y * AT, b0 = blockIdx.z * AT;
+    const long long ib = (long long)sx * chunk, ie = min(n, ib + chunk);
+    const int t = threadIdx.x, ty = t / 16, tx = t % 16;
+    float acc[4][4] = {};
+    for (long long i0 = ib; i0 < ie; i0 += KI) {
+        for (int q = t; q < AT * KI; q += 256) {
+            int r = q / KI, ii = q - r * KI;
+            long long i = i0 + ii;
+            bool ok = i < ie;
+            As[ii][r] = (ok && a0 + r < ka) ? A[(long long)(a0 + r) * lda + i] : 0.f;
+            float bv = (ok && b0 + r < kb) ? Bm[(long long)(b0 + r) * ldb + i] : 0.f;
+            if (w && ok) bv *= w[i];
+            Bs[ii][r] = bv;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int ii = 0; ii < KI; ++ii) {
+            float av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { av[u] = As[ii][ty * 4 + u]; bv[u] = Bs[ii][tx * 4 + u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            int a = a0 + ty * 4 + u, b = b0 + tx * 4 + v;
+            if (a < ka && b < kb) part[((long long)sx * ka + a) * kb + b] = (double)acc[u][v];
+        }
+}
+
+__global__ void atb_reduce(const double *__restrict__ part, int nsplit, int nab, double *__restrict__ out,
+                           long long ldo, int kb)
+{
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nab) return;
+    double s = 0.0;
+    for (int sx = 0; sx < nsplit; ++sx) s += part[(long long)sx * nab + q];
+    int a = q / kb, b = q - a * kb;
+    out[(long long)a * ldo + b] = s;
+}
+
+// out[c][i] = sum_a coef[c][a] row_a[i] + beta * dw[i] * Xc[c][i]  for c in [c0, c0 + cn)
+// rows a < k1 from A1, the rest from A2 (row stride lda)
+template <int CB>
+__global__ void __launch_bounds__(128) combine_kernel(const float *__restrict__ A1, const float *__restrict__ A2,
+                                                      int k1, int ktot, long long lda,
+                                                      const float *__restrict__ coef, int c0, int cn,
+                                                      long long n, float *__restrict__ out, long long ldo,
+                                                      const float *__restrict__ dw, const float *__restrict__ Xc,
+                                                      long long ldx, float beta)
+{
+    extern __shared__ float4 cs4[];   // [ktot][CB/4]
+    float *cs = reinterpret_cast<float *>(cs4);
+    for (int q = threadIdx.x; q < ktot * CB; q += blockDim.x) {
+        int a = q / CB, cc = q - a * CB;
+        cs[q] = cc < cn ? coef[(long long)(c0 + cc) * ktot + a] : 0.f;
+    }
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float acc[CB];
+#pragma unroll
+        for (int cc = 0; cc < CB; ++cc) acc[cc] = 0.f;
+        for (int a = 0; a < ktot; ++a) {
+            const float *row = a < k1 ? A1 + (long long)a * lda : A2 + (long long)(a - k1) * lda;
+            float v = __ldg(row + i);
+            const float4 *c4 = cs4 + a * (CB / 4);
+#pragma unroll
+            for (int q = 0; q < CB / 4; ++q) {
+                float4 c = c4[q];
+                acc[4 * q + 0] = fmaf(c.x, v, acc[4 * q + 0]);
+                acc[4 * q + 1] = fmaf(c.y, v, acc[4 * q + 1]);
+                acc[4 * q + 2] = fmaf(c.z, v, acc[4 * q + 2]);
+                acc[4 * q + 3] = fmaf(c.w, v, acc[4 * q + 3]);
+            }
+        }
+        float d = (beta != 0.f) ? beta * dw[i] : 0.f;
+#pragma unroll
+        for (int cc = 0; cc < CB; ++cc) {
+            if (cc < cn) {
+                float r = acc[cc];
+                if (beta != 0.f) r = fmaf(d, Xc[(long long)(c0 + cc) * ldx + i], r);
+                out[(long long)(c0 + cc) * ldo + i] = r;
+            }
+        }
+    }
+}
+
+__global__ void mul_kernel(const float *__restrict__ a, const float *__restrict__ b, long long n,
+                           float *__restrict__ out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = a[i] * b[i];
+}
+
+// Compact-form middle product for each column c of T ([2k][p]: rows 0..k-1
+// S^T x_c, rows k..2k-1 (B0 Y)^T x_c):
+//   cv = R^-1 a, top = R^-T ((D + gamma Y^T B0 Y) cv - gamma t2)
+//   coef[c] = [top, -gamma cv]
+__global__ void middle_kernel(const double *__restrict__ T, const double *__restrict__ SY,
+                              const double *__restrict__ YBY, int k, int kmax, int p, double gamma,
+                              double *__restrict__ scratch, float *__restrict__ coef)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= p) return;
+    double *cv = scratch + (long long)c * 2 * k, *d = cv + k;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = T[(long long)i * p + c];
+        for (int j = i + 1; j < k; ++j) s -= SY[(long long)i * kmax + j] * cv[j];
+        cv[i] = s / SY[(long long)i * kmax + i];
+    }
+    for (int i = 0; i < k; ++i) {
+        double s = SY[(long long)i * kmax + i] * cv[i];
+        double t = 0.0;
+        for (int j = 0; j < k; ++j) t += YBY[(long long)i * kmax + j] * cv[j];
+        d[i] = s + gamma * t - gamma * T[(long long)(k + i) * p + c];
+    }
+    // R^T top = d (forward substitution); overwrite d with top
+    for (int i = 0; i < k; ++i) {
+        double s = d[i];
+        for (int j = 0; j < i; ++j) s -= SY[(long long)j * kmax + i] * d[j];
+        d[i] = s / SY[(long long)i * kmax + i];
+    }
+    for (int i = 0; i < k; ++i) {
+        coef[(long long)c * 2 * k + i] = (float)d[i];
+        coef[(long long)c * 2 * k + k + i] = (float)(-gamma * cv[i]);
+    }
+}
+
+// Cholesky G = R^T R (R upper, p x p, FP64, in global scratch), then
+// coef = R^-T (lower) as FP32 for the row combination Q = R^-T E.
+__global__ void chol_kernel(const double *__restrict__ G, int p, double *__restrict__ A, double *__restrict__ R,
+                            double *__restrict__ Rinv, float *__restrict__ coef, int *__restrict__ flag)
+{
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int q = t; q < p * p; q += nt) { A[q] = G[q]; R[q] = 0.0; }
+    __syncthreads();
+    __shared__ double piv;
+    for (int j = 0; j < p; ++j) {
+        if (t == 0) {
+            double dj = A[(long long)j * p + j];
+            if (!(dj > 0.0) || !isfinite(dj)) { *flag = 1; dj = 1.0; }
+            piv = sqrt(dj);
+            R[(long long)j * p + j] = piv;
+        }
+        __syncthreads();
+        for (int i = j + 1 + t; i < p; i += nt) R[(long long)j * p + i] = A[(long long)j * p + i] / piv;
+        __syncthreads();
+        int m = p - j - 1;
+        for (int q = t; q < m * m; q += nt) {
+            int r = j + 1 + q / m, c = j + 1 + q % m;
+            if (c >= r) A[(long long)r * p + c] -= R[(long long)j * p + r] * R[(long long)j * p + c];
+        }
+        __syncthreads();
+    }
+    // R^-1 by back substitution, one column per thread
+    for (int c = t; c < p; c += nt) {
+        for (int i = p - 1; i >= 0; --i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int j = i + 1; j < p; ++j) s -= R[(long long)i * p + j] * Rinv[(long long)j * p + c];
+            Rinv[(long long)i * p + c] = s / R[(long long)i * p + i];
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < p * p; q += nt) {
+        int a = q / p, b = q % p;
+        coef[q] = (float)Rinv[(long long)b * p + a];   // (R^-T)[a][b]
+    }
+}
+
+// Omega from Omega (Q^T X) = Q^T E with Q^T E = R2 R1 (CholeskyQR2), its
+// symmetric part's eigendecomposition by parallel cyclic Jacobi
+// (round-robin pairs), eigenpairs ordered by |lambda| descending.
+// work: >= 4 p^2 + 4 p doubles; outputs lam[rank] FP64 and coef[rank][p] = U^T.
+__global__ void omega_eig_kernel(const double *__restrict__ R1, const double *__restrict__ R2,
+                                 const double *__restrict__ M1, int p, int rank, double *__restrict__ work,
+                                 double *__restrict__ lam, float *__restrict__ coef, int *__restrict__ flag,
+                                 int max_sweeps)
+{
+    const int t = threadIdx.x, nt = blockDim.x;
+    double *Aug = work;                     // [p][2p]: [M1^T | Rt^T]
+    double *A = Aug + 2LL * p * p;          // [p][p] symmetric matrix
+    double *U = A + (long long)p * p;       // [p][p]
+    double *cs = U + (long long)p * p;      // [p] cos / sin pairs (2 per pair)
+    __shared__ int piv_row;
+    __shared__ double off_sh, tot_sh;
+    // Rt = R2 R1 ; Aug = [M1^T | Rt^T]
+    for (int q = t; q < p * p; q += nt) {
+        int i = q / p, j = q % p;
+        double s = 0.0;
+        for (int l = i; l <= j; ++l) s += R2[(long long)i * p + l] * R1[(long long)l * p + j];
+        Aug[(long long)j * 2 * p + p + i] = s;                    // Rt^T[j][i]
+        Aug[(long long)i * 2 * p + j] = M1[(long long)j * p + i]; // M1^T[i][j]
+    }
+    __syncthreads();
+    // Gauss-Jordan with partial pivoting: M1^T Omega^T = Rt^T
+    for (int j = 0; j < p; ++j) {
+        if (t == 0) {
+            int best = j;
+            double bv = fabs(Aug[(long long)j * 2 * p + j]);
+            for (int r = j + 1; r < p; ++r) {
+                double v = fabs(Aug[(long long)r * 2 * p + j]);
+                if (v > bv) { bv = v; best = r; }
+            }
+            if (!(bv > 0.0)) *flag = 1;
+            piv_row = best;
+        }
+        __syncthreads();
+        int pr = piv_row;
+        if (pr != j)
+            for (int c = t; c < 2 * p; c += nt) {
+                double a = Aug[(long long)j * 2 * p + c];
+                Aug[(long long)j * 2 * p + c] = Aug[(long long)pr * 2 * p + c];
+                Aug[(long long)pr * 2 * p + c] = a;
+            }
+        __syncthreads();
+        double d = Aug[(long long)j * 2 * p + j];
+        if (d == 0.0) d = 1.0;
+        __syncthreads();
+        for (int c = t; c < 2 * p; c += nt) Aug[(long long)j * 2 * p + c] /= d;
+        __syncthreads();
+        for (int q = t; q < p * 2 * p; q += nt) {
+            int r = q / (2 * p), c = q % (2 * p);
+            if (r == j || c == j) continue;
+            Aug[(long long)r * 2 * p + c] -= Aug[(long long)r * 2 * p + j] * Aug[(long long)j * 2 * p + c];
+        }
+        __syncthreads();
+        for (int r = t; r < p; r += nt)
+            if (r != j) Aug[(long long)r * 2 * p + j] = 0.0;
+        __syncthreads();
+    }
+    // Omega^T = Aug[:, p:];  A = (Omega + Omega^T) / 2,  U = I
+    for (int q = t; q < p * p; q += nt) {
+        int i = q / p, j = q % p;
+        double oij = Aug[(long long)j * 2 * p + p + i];   // Omega[i][j] = Omega^T[j][i]
+        double oji = Aug[(long long)i * 2 * p + p + j];
+        A[q] = 0.5 * (oij + oji);
+        U[q] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int P = (p + 1) & ~1;             // even number of slots (one dummy if p is odd)
+    const int npair = P / 2;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        if (t == 0) { off_sh = 0.0; tot_sh = 0.0; }
+        __syncthreads();
+        double off = 0.0, tot = 0.0;
+        for (int q = t; q < p * p; q += nt) {
+            int i = q / p, j = q % p;
+            double v = A[q] * A[q];
+            tot += v;
+            if (i != j) off += v;
+        }
+        atomicAdd(&off_sh, off);
+        atomicAdd(&tot_sh, tot);
+        __syncthreads();
+        if (off_sh <= 1e-30 * tot_sh || off_sh == 0.0) break;
+        __syncthreads();
+        for (int round = 0; round < P - 1; ++round) {
+            // round-robin pairing: slot 0 fixed, slots 1..P-1 rotate
+            for (int m = t; m < npair; m += nt) {
+                int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
+                int b = 1 + (P - 2 - m + round) % (P - 1);
+                double c = 1.0, s = 0.0;
+                if (a < p && b < p) {
+                    int pp = min(a, b), qq = max(a, b);
+                    double apq = A[(long long)pp * p + qq];
+                    if (apq != 0.0) {
+                        double tau = (A[(long long)qq * p + qq] - A[(long long)pp * p + pp]) / (2.0 * apq);
+                        double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + tt * tt);
+                        s = tt * c;
+                    }
+                }
+                cs[2 * m] = c;
+                cs[2 * m + 1] = s;
+            }
+            __syncthreads();
+            // rows: A <- J^T A
+            for (int q = t; q < npair * p; q += nt) {
+                int m = q / p, l = q % p;
+                int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
+                int b = 1 + (P - 2 - m + round) % (P - 1);
+                if (a >= p || b >= p) continue;
+                int pp = min(a, b), qq = max(a, b);
+                double c = cs[2 * m], s = cs[2 * m + 1];
+                double x = A[(long long)pp * p + l], y = A[(long long)qq * p + l];
+                A[(long long)pp * p + l] = c * x - s * y;
+                A[(long long)qq * p + l] = s * x + c * y;
+            }
+            __syncthreads();
+            // columns: A <- A J, U <- U J
+            for (int q = t; q < npair * p; q += nt) {
+                int m = q / p, l = q % p;
+                int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
+                int b = 1 + (P - 2 - m + round) % (P - 1);
+                if (a >= p || b >= p) continue;
+                int pp = min(a, b), qq = max(a, b);
+                double c = cs[2 * m], s = cs[2 * m + 1];
+                double x = A[(long long)l * p + pp], y = A[(long long)l * p + qq];
+                A[(long long)l * p + pp] = c * x - s * y;
+                A[(long long)l * p + qq] = s * x + c * y;
+                double u = U[(long long)l * p + pp], v = U[(long long)l * p + qq];
+                U[(long long)l * p + pp] = c * u - s * v;
+                U[(long long)l * p + qq] = s * u + c * v;
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        // selection by |lambda| descending (stable: smaller index first on ties)
+        int *used = reinterpret_cast<int *>(cs);
+        for (int i = 0; i < p; ++i) used[i] = 0;
+        for (int r = 0; r < rank; ++r) {
+            int best = -1;
+            double bv = -1.0;
+            for (int i = 0; i < p; ++i) {
+                if (used[i]) continue;
+                double v = fabs(A[(long long)i * p + i]);
+                if (v > bv) { bv = v; best = i; }
+            }
+            used[best] = 1;
+            lam[r] = A[(long long)best * p + best];
+            for (int a2 = 0; a2 < p; ++a2) coef[(long long)r * p + a2] = (float)U[(long long)a2 * p + best];
+        }
+    }
+}
+
+__global__ void std_kernel(const float *__restrict__ V, const double *__restrict__ lam, int rank,
+                           const float *__restrict__ B0, long long n, float eps, float *__restrict__ out)
+{
+    __shared__ float sl[256];
+    for (int r = threadIdx.x; r < rank; r += blockDim.x) sl[r] = (float)lam[r];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float s = B0[i];
+        for (int r = 0; r < rank; ++r) {
+            float v = V[(long long)r * n + i];
+            s = fmaf(sl[r] * v, v, s);
+        }
+        out[i] = sqrtf(eps * fmaxf(s, 0.f));
+    }
+}
+
+// Philox4x32-10 (Salmon et al. 2011) + Box-Muller on 24-bit uniforms
+__device__ __forceinline__ void philox10(unsigned c[4], unsigned k0, unsigned k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        unsigned hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+        unsigned hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+        unsigned n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+__global__ void philox_normal_kernel(float *__restrict__ X, long long total, unsigned long long seed)
+{
+    const float two_pi = 6.28318530717958647692f;
+    for (long long blk = blockIdx.x * (long long)blockDim.x + threadIdx.x; blk * 4 < total;
+         blk += (long long)gridDim.x * blockDim.x) {
+        unsigned c[4] = {(unsigned)(blk & 0xFFFFFFFFull), (unsigned)(blk >> 32), 0u, 0u};
+        philox10(c, (unsigned)(seed & 0xFFFFFFFFull), (unsigned)(seed >> 32));
+#pragma unroll
+        for (int pr = 0; pr < 2; ++pr) {
+            float u1 = ((float)(c[2 * pr] >> 8) + 1.0f) * (1.0f / 16777216.0f);
+            float u2 = (float)(c[2 * pr + 1] >> 8) * (1.0f / 16777216.0f);
+            float rad = sqrtf(-2.0f * logf(u1));
+            float sn, cn;
+            sincosf(two_pi * u2, &sn, &cn);
+            long long e = blk * 4 + 2 * pr;
+            if (e < total) X[e] = rad * cn;
+            if (e + 1 < total) X[e + 1] = rad * sn;
+        }
+    }
+}
+
+int grid_n(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 8); }
+
+// C[a][b] = sum_i A[a][i] w[i] Bm[b][i] -> out (device FP64, row stride ldo)
+int atb(gbfwi_bfgs *h, const float *A, long long lda, int ka, const float *Bm, long long ldb, int kb,
+        const float *w, double *out, long long ldo, cudaStream_t s)
+{
+    if (ka == 0 || kb == 0) return GBFWI_OK;
+    const long long n = h->n;
+    long long nsplit = std::min<long long>(304, std::max<long long>(1, (n + 4095) / 4096));
+    long long chunk = ((n + nsplit - 1) / nsplit + KI - 1) / KI * KI;
+    nsplit = (n + chunk - 1) / chunk;
+    GB_TRY(h->part.ensure((size_t)nsplit * ka * kb * sizeof(double)));
+    dim3 grid((unsigned)nsplit, (ka + AT - 1) / AT, (kb + AT - 1) / AT);
+    atb_partial<<<grid, 256, 0, s>>>(A, lda, ka, Bm, ldb, kb, w, n, chunk, h->part.as<double>());
+    GB_CUDA(cudaGetLastError());
+    int nab = ka * kb;
+    atb_reduce<<<(nab + 255) / 256, 256, 0, s>>>(h->part.as<double>(), (int)nsplit, nab, out, ldo, kb);
+    GB_CUDA(cudaGetLastError());
+    return GBFWI_OK;
+}
+
+// out[c] = sum_a coef[c][a] row_a + beta * dw * Xc[c], c < nc
+int combine(gbfwi_bfgs *h, const float *A1, const float *A2, int k1, int ktot, const float *coef, int nc,
+            float *out, const float *dw, const float *Xc, float beta, cudaStream_t s)
+{
+    const long long n = h->n;
+    for (int c0 = 0; c0 < nc; c0 += 64) {
+        int cn = std::min(64, nc - c0);
+        size_t smem = (size_t)std::max(ktot, 1) * 64 * sizeof(float);
+        if (cn <= 16) {
+            smem = (size_t)std::max(ktot, 1) * 16 * sizeof(float);
+            if (smem > 48 * 1024)
+                GB_CUDA(cudaFuncSetAttribute(combine_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            combine_kernel<16><<<grid_n(n) / 2 + 1, 128, smem, s>>>(A1, A2, k1, ktot, n, coef, c0, cn, n, out, n, dw,
+                                                                  Xc, n, beta);
+        } else if (cn <= 32) {
+            smem = (size_t)std::max(ktot, 1) * 32 * sizeof(float);
+            if (smem > 48 * 1024)
+                GB_CUDA(cudaFuncSetAttribute(combine_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            combine_kernel<32><<<grid_n(n) / 2 + 1, 128, smem, s>>>(A1, A2, k1, ktot, n, coef, c0, cn, n, out, n, dw,
+                                                                  Xc, n, beta);
+        } else {
+            if (smem > 48 * 1024)
+                GB_CUDA(cudaFuncSetAttribute(combine_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            combine_kernel<64><<<grid_n(n) / 2 + 1, 128, smem, s>>>(A1, A2, k1, ktot, n, coef, c0, cn, n, out, n, dw,
+                                                                  Xc, n, beta);
+        }
+        GB_CUDA(cudaGetLastError());
+    }
+    return GBFWI_OK;
+}
+
+int stage_in(DevBuf &buf, const float *user, size_t count, cudaStream_t s, const float **dptr)
+{
+    if (gb_is_device_ptr(user)) { *dptr = user; return GBFWI_OK; }
+    GB_TRY(buf.ensure(count * sizeof(float)));
+    GB_CUDA(cudaMemcpyAsync(buf.p, user, count * sizeof(float), cudaMemcpyHostToDevice, s));
+    *dptr = buf.as<float>();
+    return GBFWI_OK;
+}
+
+// FP64 scratch of apply_dev (T and per-column vectors), placed first in `small`
+size_t small_apply_doubles(const gbfwi_bfgs *h, int p) { return (size_t)4 * std::max(h->k, 1) * p + 64; }
+
+// Size the scratch buffers once per call so that nothing is reallocated
+// while kernels queued earlier in the same call may still use it.
+int reserve(gbfwi_bfgs *h, int p, bool lowrank)
+{
+    const long long n = h->n;
+    long long nsplit = std::min<long long>(304, std::max<long long>(1, (n + 4095) / 4096));
+    size_t ab = std::max<size_t>({(size_t)(h->k + 1) * 2, (size_t)std::max(h->k, 1) * p, (size_t)p * p});
+    GB_TRY(h->part.ensure((size_t)(nsplit + 1) * ab * sizeof(double)));
+    size_t pp = (size_t)p * p;
+    size_t sm = small_apply_doubles(h, p) + (lowrank ? pp * 10 + 8 * (size_t)p + 64 : 0);
+    sm = std::max(sm, (size_t)(4 * (h->k + 1) + 8));
+    GB_TRY(h->small.ensure(sm * sizeof(double)));
+    GB_TRY(h->coef.ensure(std::max<size_t>({pp, (size_t)p * 2 * std::max(h->k, 1), 16}) * sizeof(float)));
+    return GBFWI_OK;
+}
+
+// Z = (H - minus_B0 gamma B0) X into the device buffer Z ([p][n])
+int apply_dev(gbfwi_bfgs *h, const float *Xd, int p, float *Zd, double gamma, int minus_B0, cudaStream_t s)
+{
+    const long long n = h->n;
+    const int k = h->k;
+    float beta = minus_B0 ? 0.f : (float)gamma;
+    if (k == 0) {
+        if (beta == 0.f) {
+            GB_CUDA(cudaMemsetAsync(Zd, 0, (size_t)p * n * sizeof(float), s));
+            return GBFWI_OK;
+        }
+        return combine(h, nullptr, nullptr, 0, 0, nullptr, p, Zd, h->B0.as<float>(), Xd, beta, s);
+    }
+    double *T = h->small.as<double>();
+    double *scr = T + 2 * k * p;
+    GB_TRY(atb(h, h->S.as<float>(), n, k, Xd, n, p, nullptr, T, p, s));
+    GB_TRY(atb(h, h->BY.as<float>(), n, k, Xd, n, p, nullptr, T + (long long)k * p, p, s));
+    middle_kernel<<<(p + 63) / 64, 64, 0, s>>>(T, h->dSY.as<double>(), h->dYBY.as<double>(), k, h->kmax, p, gamma,
+                                               scr, h->coef.as<float>());
+    GB_CUDA(cudaGetLastError());
+    return combine(h, h->S.as<float>(), h->BY.as<float>(), k, 2 * k, h->coef.as<float>(), p, Zd,
+                   h->B0.as<float>(), Xd, beta, s);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+
+extern "C" int gbfwi_bfgs_create(long long n, int kmax, const float *B0, gbfwi_bfgs **out)
+{
+    if (n < 1 || kmax < 1 || kmax > 4096 || !B0 || !out) return GBFWI_EINVAL;
+    gbfwi_bfgs *h = new (std::nothrow) gbfwi_bfgs();
+    if (!h) return GBFWI_ENOMEM;
+    h->n = n;
+    h->kmax = kmax;
+    int rc = h->S.ensure((size_t)kmax * n * sizeof(float));
+    if (!rc) rc = h->Y.ensure((size_t)kmax * n * sizeof(float));
+    if (!rc) rc = h->BY.ensure((size_t)kmax * n * sizeof(float));
+    if (!rc) rc = h->B0.ensure((size_t)n * sizeof(float));
+    if (!rc) rc = h->dSY.ensure((size_t)kmax * kmax * sizeof(double));
+    if (!rc) rc = h->dYBY.ensure((size_t)kmax * kmax * sizeof(double));
+    if (!rc) rc = h->flag.ensure(16);
+    if (rc) { delete h; return rc; }
+    h->SY.assign((size_t)kmax * kmax, 0.0);
+    h->YBY.assign((size_t)kmax * kmax, 0.0);
+    cudaMemcpyKind kind = gb_is_device_ptr(B0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpy(h->B0.p, B0, (size_t)n * sizeof(float), kind) != cudaSuccess) {
+        gb_set_last_cuda_error(cudaGetLastError(), "copy B0", __FILE__, __LINE__);
+        delete h;
+        return GBFWI_ECUDA;
+    }
+    *out = h;
+    return GBFWI_OK;
+}
+
+extern "C" int gbfwi_bfgs_destroy(gbfwi_bfgs *h)
+{
+    delete h;
+    return GBFWI_OK;
+}
+
+extern "C" int gbfwi_bfgs_count(const gbfwi_bfgs *h) { return h ? h->k : GBFWI_EINVAL; }
+
+extern "C" int gbfwi_bfgs_update(gbfwi_bfgs *h, const float *s_, const float *y_, void *stream)
+{
+    if (!h || !s_ || !y_) return GBFWI_EINVAL;
+    if (h->k >= h->kmax) return GBFWI_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = h->n;
+    const int k = h->k;
+    float *sk = h->S.as<float>() + (long long)k * n;
+    float *yk = h->Y.as<float>() + (long long)k * n;
+    float *byk = h->BY.as<float>() + (long long)k * n;
+    GB_CUDA(cudaMemcpyAsync(sk, s_, n * sizeof(float), gb_is_device_ptr(s_) ? cudaMemcpyDeviceToDevice
+                                                                              : cudaMemcpyHostToDevice, s));
+    GB_CUDA(cudaMemcpyAsync(yk, y_, n * sizeof(float), gb_is_device_ptr(y_) ? cudaMemcpyDeviceToDevice
+                                                                              : cudaMemcpyHostToDevice, s));
+    mul_kernel<<<grid_n(n), 256, 0, s>>>(h->B0.as<float>(), yk, n, byk);
+    GB_CUDA(cudaGetLastError());
+    // dots: s_i^T [y_k, s_k] (i <= k), (B0 y_i)^T y_k (i <= k), y_k^T y_k
+    GB_TRY(reserve(h, 1, false));
+    double *d1 = h->small.as<double>();          // [(k+1)][2]
+    double *d2 = d1 + 2 * (k + 1);               // [(k+1)]
+    double *d3 = d2 + (k + 1);                   // [1]
+    GB_TRY(atb(h, h->S.as<float>(), n, k + 1, yk, n, 1, nullptr, d1, 2, s));
+    GB_TRY(atb(h, h->S.as<float>(), n, k + 1, sk, n, 1, nullptr, d1 + 1, 2, s));
+    GB_TRY(atb(h, h->BY.as<float>(), n, k + 1, yk, n, 1, nullptr, d2, 1, s));
+    GB_TRY(atb(h, yk, n, 1, yk, n, 1, nullptr, d3, 1, s));
+    std::vector<double> hd(4 * (k + 1) + 1);
+    GB_CUDA(cudaMemcpyAsync(hd.data(), d1, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    double ys = hd[2 * k], ss = hd[2 * k + 1], yy = hd[2 * (k + 1) + (k + 1)];
+    if (!std::isfinite(ys) || !std::isfinite(ss) || !std::isfinite(yy)) return GBFWI_ENONFINITE;
+    if (!(ys > 1e-12 * std::sqrt(ss) * std::sqrt(yy))) return GBFWI_ECURV;
+    const int km = h->kmax;
+    for (int i = 0; i <= k; ++i) {
+        h->SY[(size_t)i * km + k] = hd[2 * i];
+        double v = hd[2 * (k + 1) + i];
+        h->YBY[(size_t)i * km + k] = v;
+        h->YBY[(size_t)k * km + i] = v;
+    }
+    GB_CUDA(cudaMemcpyAsync(h->dSY.p, h->SY.data(), h->SY.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    GB_CUDA(cudaMemcpyAsync(h->dYBY.p, h->YBY.data(), h->YBY.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    h->k = k + 1;
+    return GBFWI_OK;
+}
+
+extern "C" int gbfwi_bfgs_apply(gbfwi_bfgs *h, const float *X, int p, float *Z, double gamma, int minus_B0,
+                                void *stream)
+{
+    if (!h || !X || !Z || p < 1 || p > 256 || !(gamma > 0)) return GBFWI_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = h->n;
+    const float *Xd;
+    GB_TRY(stage_in(h->X, X, (size_t)p * n, s, &Xd));
+    GB_TRY(reserve(h, p, false));
+    const bool dev_out = gb_is_device_ptr(Z);
+    float *Zd = Z;
+    if (!dev_out) {
+        GB_TRY(h->E.ensure((size_t)p * n * sizeof(float)));
+        Zd = h->E.as<float>();
+    }
+    GB_TRY(apply_dev(h, Xd, p, Zd, gamma, minus_B0, s));
+    if (!dev_out) {
+        GB_CUDA(cudaMemcpyAsync(Z, Zd, (size_t)p * n * sizeof(float), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+    }
+    return GBFWI_OK;
+}
+
+extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int rank, unsigned long long seed,
+                                     double eps_prior, float *V, double *lambda, float *std_out, void *stream)
+{
+    if (!h || p < 1 || p > 256 || rank < 1 || rank > p || !(eps_prior > 0)) return GBFWI_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = h->n;
+    const float *Xd;
+    if (X) {
+        GB_TRY(stage_in(h->X, X, (size_t)p * n, s, &Xd));
+    } else {
+        GB_TRY(h->X.ensure((size_t)p * n * sizeof(float)));
+        philox_normal_kernel<<<grid_n((p * n + 3) / 4), 256, 0, s>>>(h->X.as<float>(), (long long)p * n, seed);
+        GB_CUDA(cudaGetLastError());
+        Xd = h->X.as<float>();
+    }
+    GB_TRY(h->E.ensure((size_t)p * n * sizeof(float)));
+    GB_TRY(h->Q.ensure((size_t)p * n * sizeof(float)));
+    GB_TRY(reserve(h, p, true));
+    float *E = h->E.as<float>(), *Q = h->Q.as<float>();
+    // 1. E = (B_{n+1} - B0) X
+    GB_TRY(apply_dev(h, Xd, p, E, 1.0, 1, s));
+    // 2. CholeskyQR2: Q = R1^-T E, Q <- R2^-T Q
+    const size_t pp = (size_t)p * p;
+    double *G, *A, *R1, *R2, *Rinv, *M1, *work, *lam;
+    G = h->small.as<double>() + small_apply_doubles(h, p);
+    A = G + pp;
+    R1 = A + pp;
+    R2 = R1 + pp;
+    Rinv = R2 + pp;
+    M1 = Rinv + pp;
+    work = M1 + pp;          // 4 pp + 4 p
+    lam = work + 4 * pp + 4 * (size_t)p;
+    float *coef = h->coef.as<float>();
+    int *flag = h->flag.as<int>();
+    GB_CUDA(cudaMemsetAsync(flag, 0, 16, s));
+    GB_TRY(atb(h, E, n, p, E, n, p, nullptr, G, p, s));
+    chol_kernel<<<1, 256, 0, s>>>(G, p, A, R1, Rinv, coef, flag);
+    GB_CUDA(cudaGetLastError());
+    GB_TRY(combine(h, E, nullptr, p, p, coef, p, Q, nullptr, nullptr, 0.f, s));
+    GB_TRY(atb(h, Q, n, p, Q, n, p, nullptr, G, p, s));
+    chol_kernel<<<1, 256, 0, s>>>(G, p, A, R2, Rinv, coef, flag);
+    GB_CUDA(cudaGetLastError());
+    GB_TRY(combine(h, Q, nullptr, p, p, coef, p, E, nullptr, nullptr, 0.f, s));   // final Q in E
+    float *Qf = E;
+    // 3. M1 = Q^T X ; Omega (Q^T X) = R2 R1 ; eigenpairs
+    GB_TRY(atb(h, Qf, n, p, Xd, n, p, nullptr, M1, p, s));
+    omega_eig_kernel<<<1, 256, 0, s>>>(R1, R2, M1, p, rank, work, lam, coef, flag, 60);
+    GB_CUDA(cudaGetLastError());
+    // 4. V = Q U (first `rank` columns)
+    const bool devV = V && gb_is_device_ptr(V);
+    float *Vd = devV ? V : Q;     // Q buffer is free now
+    GB_TRY(combine(h, Qf, nullptr, p, p, coef, rank, Vd, nullptr, nullptr, 0.f, s));
+    // 5. posterior std (Eq. 14)
+    if (std_out) {
+        bool devS = gb_is_device_ptr(std_out);
+        float *Sd = devS ? std_out : Qf;   // E buffer free after V
+        std_kernel<<<grid_n(n), 256, 0, s>>>(Vd, lam, rank, h->B0.as<float>(), n, (float)eps_prior, Sd);
+        GB_CUDA(cudaGetLastError());
+        if (!devS) GB_CUDA(cudaMemcpyAsync(std_out, Sd, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    }
+    if (V && !devV) GB_CUDA(cudaMemcpyAsync(V, Vd, (size_t)rank * n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (lambda)
+        GB_CUDA(cudaMemcpyAsync(lambda, lam, rank * sizeof(double),
+                                gb_is_device_ptr(lambda) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    int flag_h = 0;
+    GB_CUDA(cudaMemcpyAsync(&flag_h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (flag_h) return GBFWI_ENONFINITE;
+    return GBFWI_OK;
+}

@@ -1,0 +1,162 @@
+// Internal declarations of the gbfwi library (sm_103a).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "gbfwi.h"
+
+#define GB_NG 5
+
+// ---------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------
+
+#define GB_CUDA(call)                                                    \
+    do {                                                                 \
+        cudaError_t _e = (call);                                         \
+        if (_e != cudaSuccess) {                                         \
+            gb_set_last_cuda_error(_e, #call, __FILE__, __LINE__);       \
+            return GBFWI_ECUDA;                                          \
+        }                                                                \
+    } while (0)
+
+#define GB_TRY(expr)                    \
+    do {                                \
+        int _rc = (expr);               \
+        if (_rc != GBFWI_OK) return _rc; \
+    } while (0)
+
+void gb_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t nbytes);          // grow-only cudaMalloc
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(p); }
+    ~DevBuf() { release(); }
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+};
+
+// true when ptr is device (or managed) memory of the current context
+bool gb_is_device_ptr(const void *ptr);
+
+// ---------------------------------------------------------------------------
+// element tiles
+// ---------------------------------------------------------------------------
+
+struct TileShape { int tx, tz; };
+static constexpr int kNumTiles = 5;
+extern const TileShape kTiles[kNumTiles];
+
+// injection entry: F_x += wx * sig[cx], F_z += wz * sig[cz]
+struct InjEntry { int cx, cz; float wx, wz; };
+// entries [begin, end) all act on owned node (ox, oz) of the tile, packed
+// as node = oz * (4 TX + 1) + ox
+struct InjGroup { int node, begin, end, pad; };
+
+struct TileLists {
+    bool built = false;
+    int ntx = 0, ntz = 0;
+    DevBuf src_gptr;     // int [nsrc][ntiles + 1]
+    DevBuf src_groups;   // InjGroup
+    DevBuf src_entries;  // InjEntry
+    DevBuf rec_gptr;     // int [ntiles + 1]   (adjoint sources at the receivers)
+    DevBuf rec_groups;
+    DevBuf rec_entries;
+    DevBuf rec_tptr;     // int [ntiles + 1]   receivers recorded by each tile
+    DevBuf rec_list;     // int receiver ids, grouped by tile
+};
+
+// ---------------------------------------------------------------------------
+// mesh handle
+// ---------------------------------------------------------------------------
+
+struct gbfwi_mesh {
+    gbfwi_mesh_desc d{};
+    int nx = 0, nz = 0, pitch = 0;      // node grid; pitch = row length in nodes (even)
+    double xi[GB_NG], w[GB_NG], D[GB_NG][GB_NG];
+    std::vector<gbfwi_source> src;
+    std::vector<double> rec_xz;
+    int nrec = 0;
+    // receivers: element and 25 interpolation weights
+    std::vector<int> rec_ex, rec_ez;
+    std::vector<float> rec_w;            // [nrec][25], index j*5+i
+    // sources: nodal weights
+    struct SrcNode { int ix, iz; float wx, wz; };
+    std::vector<std::vector<SrcNode>> src_nodes;
+    // assembled 1-D quadrature weights (metres): W_g = wx[ix] * wz[iz]
+    std::vector<double> wx1, wz1;
+    gbfwi_schedule sch{1, 0, 0, 0};
+    bool have_model = false;
+    double dx_min = 0;                   // smallest GLL node spacing
+
+    // device tables
+    DevBuf d_lm;        // float2 [nz][pitch]  (lambda, mu)
+    DevBuf d_minv;      // float  [nz][pitch]  1 / M
+    DevBuf d_bnd;       // float4 [nz][pitch]  (Cx, Cz, 1/(M + dt/2 Cx), 1/(M + dt/2 Cz)); edges only
+    DevBuf d_bw;        // float4 [nz][pitch]  (Wn_x, Wn_z, Wt_x, Wt_z) Stacey edge weights
+    DevBuf d_model;     // float  [3][nz][pitch] rho, vp, vs
+    DevBuf d_wx, d_wz;  // float  [nx], [nz]
+    DevBuf d_recw;      // float  [nrec][25]
+    DevBuf d_rec_e;     // int2   [nrec] element (ex, ez)
+    DevBuf d_stf;       // float  [nsrc][nt + 1]
+    TileLists lists[kNumTiles];
+
+    // work buffers (grown on demand)
+    DevBuf w_hist, w_vh, w_adj, w_wh, w_acc, w_snap, w_seis, w_sig, w_obs, w_grad,
+        w_red, w_flag, w_shots, w_tmp, w_stage;
+    DevBuf w_pc;        // preconditioner accumulators
+};
+
+int gb_build_tile_lists(gbfwi_mesh *m, int tile);
+
+// ---------------------------------------------------------------------------
+// kernel argument block of the time step (one launch = one step of every
+// shot of a batch)
+// ---------------------------------------------------------------------------
+
+enum StepMode { MODE_FWD = 0, MODE_FWD_PC = 1, MODE_ADJ_G = 2, MODE_ADJ_PC = 3 };
+
+struct StepArgs {
+    int nex, nez, nx, nz, pitch;
+    float dt;
+    long long fstride;            // float2 elements between shots of every field
+                                  // (fields are stored [slot][shot][nz][pitch])
+    const float2 *ucur;           // u_{n+1} (read, window)
+    float2 *unext;                // u_{n+2} (written, owned nodes)
+    float2 *vh;                   // half-step velocity, in place (owned nodes)
+    const float2 *uold;           // level n of the same field (P-modes)
+    long long hstride;            // float2 elements between shots of the history (= fstride)
+    const float2 *h0, *h1, *h2;   // forward history levels (adjoint modes)
+    const float2 *lm;
+    const float *minv;
+    const float4 *bnd;
+    const float4 *bw;
+    const float *wxs, *wzs;
+    // injection
+    const int *gptr; const InjGroup *groups; const InjEntry *entries;
+    int per_shot_groups;          // 1: groups indexed by source id
+    int ntiles;
+    const float *sig; long long sig_shot_stride; int sig_chan_stride; int tsig; float sig_scale;
+    const int *shot_map;          // batch slot -> source id (or nullptr: identity)
+    // recording
+    const int *rec_tptr, *rec_list; const float *recw; const int2 *rec_e;
+    float *seis; long long seis_shot_stride; int nt; int trec;
+    // accumulators
+    float *acc; long long acc_shot_stride; long long acc_comp_stride;
+};
+
+int gb_launch_step(int mode, int tile, const StepArgs &a, int nbatch, cudaStream_t s);
+
+// small kernels of the SEM driver
+int gb_material(gbfwi_mesh *m, cudaStream_t s);

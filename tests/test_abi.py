@@ -1,0 +1,82 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+include/gbfwi.h declares; host-only calls behave without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2009_12663_gb300 as gb
+from paper_2009_12663_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "gbfwi.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(gbfwi_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_header_lists_match_binding():
+    assert sorted(_lib.ABI_SYMBOLS) == _declared()
+
+
+def test_library_exports_every_declared_symbol():
+    L = gb.lib()
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_library_is_sm103a_and_in_tree():
+    from paper_2009_12663_gb300 import build
+    path = build.build()
+    assert os.path.commonpath([path, ROOT]) == ROOT
+    assert "compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_strerror_and_tiles_host_only():
+    L = gb.lib()
+    assert L.gbfwi_strerror(0) == b"ok"
+    assert b"curvature" in L.gbfwi_strerror(-5)
+    assert L.gbfwi_strerror(12345) == b"unknown error"
+    assert gb.num_tiles() >= 1
+    for t in range(gb.num_tiles()):
+        tx, tz = gb.tile_shape(t)
+        assert tx >= 1 and tz >= 1 and ((tx + 1) * (tz + 1)) % 32 == 0
+    with pytest.raises(gb.GbfwiError):
+        gb.tile_shape(gb.num_tiles())
+
+
+def test_mesh_create_rejects_bad_arguments_before_any_device_call():
+    src = [dict(x=10.0, z=10.0, type=0, f0=10.0)]
+    rec = np.array([[5.0, 0.0]])
+    bad = [
+        dict(nex=0, nez=4, h=10.0, dt=1e-3, nt=10),      # no elements
+        dict(nex=4, nez=4, h=-1.0, dt=1e-3, nt=10),      # negative size
+        dict(nex=4, nez=4, h=10.0, dt=0.0, nt=10),       # zero dt
+        dict(nex=4, nez=4, h=10.0, dt=1e-3, nt=1),       # too few steps
+    ]
+    for kw in bad:
+        with pytest.raises(gb.GbfwiError) as e:
+            gb.Mesh(kw["nex"], kw["nez"], kw["h"], kw["dt"], kw["nt"], src, rec)
+        assert e.value.name == "EINVAL"
+    # source outside the mesh
+    with pytest.raises(gb.GbfwiError) as e:
+        gb.Mesh(4, 4, 10.0, 1e-3, 10, [dict(x=100.0, z=10.0, f0=10.0)], rec)
+    assert e.value.name == "EINVAL"
+    # bad source type
+    with pytest.raises(gb.GbfwiError) as e:
+        gb.Mesh(4, 4, 10.0, 1e-3, 10, [dict(x=10.0, z=10.0, type=7, f0=10.0)], rec)
+    assert e.value.name == "EINVAL"
+
+
+def test_null_handles_rejected():
+    L = gb.lib()
+    assert L.gbfwi_mesh_dims(None, None, None) == -1
+    assert L.gbfwi_bfgs_count(None) == -1
+    assert L.gbfwi_forward(None, None, 0, None, None) == -1
+    assert L.gbfwi_bfgs_apply(None, None, 1, None, ctypes.c_double(1.0), 0, None) == -1
+    assert L.gbfwi_mesh_destroy(None) == 0
+    assert L.gbfwi_bfgs_destroy(None) == 0

@@ -1,0 +1,201 @@
+"""GPU parity of the spectral-element path (forward, misfit + gradient,
+preconditioners) against the FP64 oracle, through the C ABI.
+
+Tolerances: seismograms and misfit 1e-4 relative L2, gradient and
+preconditioner maps 1e-3 relative L2 per parameter.  The mesh (40 x 20
+elements) spans several tiles of every tile shape with a ragged last tile.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import sem as osem
+
+torch = pytest.importorskip("torch")
+import paper_2009_12663_gb300 as gb  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def t32(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float32, device=DEV)
+
+
+class Case:
+    """Workload + oracle results, computed once per module."""
+
+    def __init__(self, wl, nshot=1, amp=1e12, seed=1):
+        self.wl = wl
+        self.st = osem.Setup(osem.Mesh(wl.nex, wl.nez, wl.h), wl.dt, wl.nt, wl.rec_xz,
+                             free_top=wl.free_top)
+        x, z = self.st.mesh.coords()
+        self.true = synth.gaussian_anomaly(x, z, seed=seed)
+        self.start = synth.homogeneous(x, z)
+        self.srcs = wl.sources(amp=amp)[:nshot]
+        self.obs = []
+        for s in self.srcs:
+            fv, stf = self.st.source(s)
+            self.obs.append(self.st.forward(self.true, fv, stf))
+        self.obs = np.stack(self.obs)
+
+    def mesh(self, **sched):
+        m = gb.Mesh(self.wl.nex, self.wl.nez, self.wl.h, self.wl.dt, self.wl.nt, self.srcs,
+                    self.wl.rec_xz, free_surface_top=self.wl.free_top)
+        if sched:
+            m.set_schedule(**sched)
+        m.set_model(*[t32(a) for a in self.start])
+        return m
+
+    def gpu_forward(self, m, ids):
+        seis = torch.zeros(len(ids), self.wl.nrec, 2, self.wl.nt, device=DEV)
+        m.forward(ids, seis)
+        torch.cuda.synchronize()
+        return seis.cpu().numpy()
+
+    def gpu_gradient(self, m, ids, ckpt=-1):
+        grad = torch.zeros(3, m.nz, m.nx, device=DEV)
+        f = m.adjoint_gradient(ids, t32(self.obs[ids]), grad, ckpt)
+        torch.cuda.synchronize()
+        return f, grad.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def c1():
+    case = Case(synth.tiny_homogeneous(1200))
+    case.f, case.g, case.syn = osem.misfit_gradient(case.st, case.start, case.srcs, list(case.obs))
+    return case
+
+
+@pytest.fixture(scope="module")
+def c2():
+    """Two shots, shorter record, free top replaced by Stacey (all edges absorb)."""
+    wl = synth.tiny_homogeneous(500)
+    wl.src_xz = np.array([[300.0, 10.0], [725.0, 60.0]])
+    wl.free_top = 0
+    case = Case(wl, nshot=2, seed=4)
+    case.f, case.g, case.syn = osem.misfit_gradient(case.st, case.start, case.srcs, list(case.obs))
+    return case
+
+
+def test_forward_matches_oracle(c1):
+    m = c1.mesh()
+    s = c1.gpu_forward(m, [0])
+    assert rel(s[0], c1.syn[0]) < 1e-4
+
+
+@pytest.mark.parametrize("tile", range(5))
+def test_forward_every_tile_shape_bitwise_equal(c1, tile):
+    base = c1.gpu_forward(c1.mesh(tile=0), [0])
+    s = c1.gpu_forward(c1.mesh(tile=tile), [0])
+    assert np.array_equal(s, base)
+
+
+def test_gradient_matches_oracle(c1):
+    f, g = c1.gpu_gradient(c1.mesh(), [0])
+    assert abs(f - c1.f) / c1.f < 1e-4
+    for c in range(3):
+        assert rel(g[c], c1.g[c]) < 1e-3, c
+
+
+def test_gradient_two_shots_all_absorbing(c2):
+    f, g = c2.gpu_gradient(c2.mesh(), [0, 1])
+    assert abs(f - c2.f) / c2.f < 1e-4
+    for c in range(3):
+        assert rel(g[c], c2.g[c]) < 1e-3, c
+
+
+def test_batched_shots_equal_single_shot_launches(c2):
+    f1, g1 = c2.gpu_gradient(c2.mesh(shots_per_launch=1), [0, 1])
+    f2, g2 = c2.gpu_gradient(c2.mesh(shots_per_launch=2), [0, 1])
+    s1 = c2.gpu_forward(c2.mesh(shots_per_launch=1), [0, 1])
+    s2 = c2.gpu_forward(c2.mesh(shots_per_launch=2), [0, 1])
+    assert np.array_equal(s1, s2)
+    assert f1 == f2 or abs(f1 - f2) <= 1e-12 * abs(f1)
+    assert np.array_equal(g1, g2)
+
+
+def test_checkpointed_gradient_equals_full_history(c1):
+    f0, g0 = c1.gpu_gradient(c1.mesh(), [0], ckpt=0)
+    for C in (97, 400):
+        f, g = c1.gpu_gradient(c1.mesh(), [0], ckpt=C)
+        assert f == f0
+        assert np.array_equal(g, g0)
+
+
+def test_gradient_is_deterministic(c1):
+    m = c1.mesh()
+    a = c1.gpu_gradient(m, [0])
+    b = c1.gpu_gradient(m, [0])
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3, 4])
+def test_preconditioner_matches_oracle(c1, kind):
+    sigma, damp = 50.0, 1.0
+    H_ref = osem.precond_raw(c1.st, c1.start, c1.srcs, kind)
+    _, B0_ref = osem.smooth_damp_invert(c1.st, H_ref, sigma, damp)
+    m = c1.mesh()
+    H = torch.zeros(3, m.nz, m.nx, device=DEV)
+    B0 = torch.zeros(3, m.nz, m.nx, device=DEV)
+    m.precond_diag([0], kind, sigma, damp, H, B0)
+    torch.cuda.synchronize()
+    H, B0 = H.cpu().numpy(), B0.cpu().numpy()
+    for c in range(3):
+        assert rel(H[c], H_ref[c]) < 1e-3, (kind, c, rel(H[c], H_ref[c]))
+        assert rel(B0[c], B0_ref[c]) < 1e-3, (kind, c)
+
+
+def test_host_buffers_match_device_buffers(c1):
+    m = c1.mesh()
+    dev_s = c1.gpu_forward(m, [0])
+    host = np.zeros((1, c1.wl.nrec, 2, c1.wl.nt), np.float32)
+    m.forward([0], host)
+    assert np.array_equal(host, dev_s)
+    gh = np.zeros((3, m.nz, m.nx), np.float32)
+    fh = m.adjoint_gradient([0], c1.obs.astype(np.float32)[:1], gh)
+    fd, gd = c1.gpu_gradient(m, [0])
+    assert fh == fd and np.array_equal(gh, gd)
+
+
+def test_single_element_mesh_and_edge_receivers():
+    """Degenerate mesh: one element, receivers on corners / edges, source on an edge."""
+    wl = synth.Workload("one element", 1, 1, 40.0, 5e-4, 200, 60.0,
+                        np.array([[40.0, 20.0]]), np.array([[0.0, 0.0], [40.0, 40.0], [20.0, 0.0], [13.0, 27.0]]))
+    case = Case(wl, amp=1e10)
+    f, g, syn = osem.misfit_gradient(case.st, case.start, case.srcs, list(case.obs))
+    m = case.mesh()
+    s = case.gpu_forward(m, [0])
+    assert rel(s[0], syn[0]) < 1e-4
+    fg, gg = case.gpu_gradient(m, [0])
+    assert abs(fg - f) / f < 1e-4
+    for c in range(3):
+        assert rel(gg[c], g[c]) < 1e-3
+
+
+def test_errors_surface_as_codes(c1):
+    m = gb.Mesh(4, 3, 25.0, 5e-4, 20, [dict(x=50.0, z=10.0, f0=20.0)], np.array([[10.0, 0.0]]))
+    seis = torch.zeros(1, 1, 2, 20, device=DEV)
+    with pytest.raises(gb.GbfwiError) as e:
+        m.forward([0], seis)                          # no model yet
+    assert e.value.name == "ENOMODEL"
+    one = np.ones((m.nz, m.nx), np.float32)
+    with pytest.raises(gb.GbfwiError) as e:
+        m.set_model(2000 * one, 9000 * one, 3000 * one)   # CFL violated
+    assert e.value.name == "ECFL"
+    bad = 3000 * one
+    bad[2, 3] = np.nan
+    with pytest.raises(gb.GbfwiError) as e:
+        m.set_model(2000 * one, bad, 1700 * one)
+    assert e.value.name == "ENONFINITE"
+    m.set_model(2000 * one, 3000 * one, 1700 * one)
+    with pytest.raises(gb.GbfwiError) as e:
+        m.forward([1], seis)                          # no such shot
+    assert e.value.name == "EINVAL"
+    with pytest.raises(gb.GbfwiError) as e:
+        m.set_schedule(tile=99)
+    assert e.value.name == "EINVAL"
