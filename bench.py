@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the preconditioned-BFGS elastic FWI hot path on GB300.
+
+One step = one FWI iteration's device work on the 340 x 70 element
+Marmousi-shaped model (17 km x 3.5 km, NGLL 5, 382,441 GLL points, 24
+explosive 5 Hz shots, 341 receivers, dt 0.5 ms, 12000 steps, one shot per
+launch):
+  set_model -> adjoint_gradient (24 x (forward + adjoint + kernel)) ->
+  bfgs_update -> lowrank_invhess (50-pair store, 60 probes, rank 50,
+  n = 3 x 382,441).
+metric: GLL-point-updates/s = 2 * shots * N_glob * nt / step time; the line
+also reports s per gradient and s per rank-k UQ.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs its own 24 shots (weak scaling); rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "GLL-point-updates/s fwd+adj+kernel (HBM % peak); s per FWI gradient; s per rank-k UQ"
+ADJ_BYTES_PER_POINT = 76       # adjoint step: w r/w 16, wh r/w 16, material 12, u_k 8, 3 accumulators r/w 24
+FWD_BYTES_PER_POINT = 44       # forward step: u r/w 16, vh r/w 16, material 12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nt", type=int, default=12000, help="time steps (12000 is the benchmark workload)")
+    ap.add_argument("--shots", type=int, default=24)
+    ap.add_argument("--tile", type=int, default=None)
+    ap.add_argument("--shots-per-launch", type=int, default=1)
+    ap.add_argument("--ckpt", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                               f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_record(kernel: str):
+    """DRAM traffic of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2009_12663_gb300", "csrc", "sem_step.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("sem_step_sha") != h:
+        return None
+    return rec
+
+
+def build_problem(args, dev_index=0):
+    wl = synth.marmousi_like_workload(nt=args.nt, nshot=args.shots)
+    return wl
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(wl, nt_sample: int, nshot: int, threads: int):
+    """The FP64 oracle on a bounded sample of the workload: `nshot` shots of
+    the full mesh over the first `nt_sample` steps, forward + adjoint +
+    gradient, shots in parallel threads.  Returns (point-updates/s, seconds)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from oracle import sem as osem
+    st = osem.Setup(osem.Mesh(wl.nex, wl.nez, wl.h), wl.dt, nt_sample, wl.rec_xz)
+    x, z = st.mesh.coords()
+    W, H = wl.nex * wl.h, wl.nez * wl.h
+    start = synth.marmousi_like_smooth(x, z, 2024, W, H)
+    srcs = wl.sources(amp=1e12)[:nshot]
+    obs = [np.zeros((wl.nrec, 2, nt_sample)) for _ in srcs]
+
+    def one(i):
+        return osem.misfit_gradient(st, start, [srcs[i]], [obs[i]])
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(one, range(len(srcs))))
+    dt = time.perf_counter() - t0
+    updates = 2.0 * len(srcs) * wl.nglob * nt_sample
+    return updates / dt, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = build_problem(args)
+    threads = max(1, min(os.cpu_count() or 1, 16))
+    nt_s, ns = 40, min(threads, wl.nshot)
+    for _ in range(args.warmup):
+        oracle_sample(wl, nt_s, ns, threads)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, s = oracle_sample(wl, nt_s, ns, threads)
+        vals.append(v)
+        secs.append(s)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GLL-point-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name + f", {wl.nshot} shots, {wl.nrec} receivers, nt {wl.nt}",
+                   "sample": f"{ns} shots x first {nt_s} steps per step (FP64 oracle, forward+adjoint+gradient)"},
+        "cpu_baseline": {"value": value, "unit": "GLL-point-updates/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{ns} shots x {nt_s} steps of the {wl.nex}x{wl.nez} mesh"},
+        "e2e": {"value": value, "unit": "GLL-point-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2009_12663_gb300 as gb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    wl = build_problem(args)
+    srcs = wl.sources(amp=1e12)
+    m = gb.Mesh(wl.nex, wl.nez, wl.h, wl.dt, wl.nt, srcs, wl.rec_xz, free_surface_top=1)
+    tile = args.tile if args.tile is not None else 0
+    m.set_schedule(shots_per_launch=args.shots_per_launch, tile=tile, use_graph=0, ckpt_every=args.ckpt)
+    x, z = m.node_coords()
+    W, H = wl.nex * wl.h, wl.nez * wl.h
+    seed = 2024 + rank
+    true = [torch.tensor(a, dtype=torch.float32, device=dev) for a in synth.marmousi_like(x, z, seed, W, H)]
+    start = [torch.tensor(a, dtype=torch.float32, device=dev) for a in synth.marmousi_like_smooth(x, z, seed, W, H)]
+    shots = list(range(wl.nshot))
+    N = m.nglob
+    n = 3 * N
+
+    # observed data from the true model (untimed)
+    m.set_model(*true)
+    d_obs = torch.zeros(wl.nshot, wl.nrec, 2, wl.nt, device=dev)
+    m.forward(shots, d_obs)
+    grad = torch.zeros(3, m.nz, m.nx, device=dev)
+
+    # BFGS stores: UQ store with 50 pairs (synthetic history at full n), and
+    # an iteration store receiving one pair per step
+    S, Y, B0 = synth.synthetic_history(77 + rank, n, 50)
+    B0d = torch.tensor(B0, device=dev)
+    uq = gb.Bfgs(n, 50, B0d)
+    for i in range(50):
+        uq.update(torch.tensor(S[i], device=dev), torch.tensor(Y[i], device=dev))
+    total_steps = args.warmup + args.steps + (0 if args.no_e2e else args.steps)
+    S2, Y2, _ = synth.synthetic_history(99 + rank, n, total_steps)
+    S2d, Y2d = torch.tensor(S2, device=dev), torch.tensor(Y2, device=dev)
+    it = gb.Bfgs(n, total_steps, B0d)
+    p, rnk = 60, 50
+    V = torch.zeros(rnk, n, device=dev)
+    lam = torch.zeros(rnk, dtype=torch.float64, device=dev)
+    std = torch.zeros(n, device=dev)
+    m.enable_timing(True)
+    stream = torch.cuda.current_stream(dev)
+    step_i = [0]
+
+    def step(timers=None):
+        i = step_i[0]
+        step_i[0] += 1
+        if timers:
+            timers[0].record(stream)
+        m.set_model(*start)
+        m.adjoint_gradient(shots, d_obs, grad)
+        if timers:
+            timers[1].record(stream)
+        it.update(S2d[i], Y2d[i])
+        uq.lowrank_invhess(p, rnk, seed=1000 + i, eps_prior=1.0, V=V, lam=lam, std=std)
+        if timers:
+            timers[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    clocks = Clocks(dev.index)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    phase = []
+    barrier()
+    l0 = gb.launch_count()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(ev[k])
+        phase.append(None)
+    t1.record(stream)
+    barrier()
+    ck = clocks.stop()
+    launches = gb.launch_count() - l0
+    ph = m.last_phase_times()
+    ms = t0.elapsed_time(t1) / args.steps
+    grad_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    uq_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    updates_per_step = 2.0 * wl.nshot * N * wl.nt
+    value = world * updates_per_step / (ms / 1e3)
+
+    # end to end through host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        h_model = [a.cpu().pin_memory() for a in start]
+        h_obs = d_obs.cpu().pin_memory()
+        h_grad = torch.zeros(3, m.nz, m.nx).pin_memory()
+        h_s = S2d.cpu().pin_memory()
+        h_y = Y2d.cpu().pin_memory()
+        h_std = torch.zeros(n).pin_memory()
+        barrier()
+        te = time.perf_counter()
+        for k in range(args.steps):
+            i = step_i[0]
+            step_i[0] += 1
+            m.set_model(*h_model)
+            m.adjoint_gradient(shots, h_obs, h_grad)
+            it.update(h_s[i], h_y[i])
+            uq.lowrank_invhess(p, rnk, seed=1000 + i, eps_prior=1.0, std=h_std)
+        barrier()
+        e2e_s = (time.perf_counter() - te) / args.steps
+        if world > 1:
+            tt = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        h2d = 3 * N * 4 + h_obs.numel() * 4 + 2 * n * 4
+        d2h = 3 * N * 4 + n * 4 + 8
+        e2e = {"value": world * updates_per_step / e2e_s, "unit": "GLL-point-updates/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    pk, pk_kind = peaks()
+    adj_bytes = ADJ_BYTES_PER_POINT * N * ph["adj_launches"]
+    achieved = adj_bytes / (ph["adj_ms"] / 1e3) / 1e9
+    fwd_achieved = FWD_BYTES_PER_POINT * N * ph["fwd_launches"] / (ph["fwd_ms"] / 1e3) / 1e9
+    tr = traffic_record("adjoint_step")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": (tr or {}).get("bytes_per_launch"),
+            "kernel": "sem_step_kernel<15,7,ADJ_G> (adjoint step + gradient correlation)",
+            "algorithmic_bytes_per_launch": ADJ_BYTES_PER_POINT * N,
+            "avg_launch_us": 1e3 * ph["adj_ms"] / ph["adj_launches"],
+            "peak_kind": pk_kind,
+            "forward_kernel": {"achieved": fwd_achieved, "frac": fwd_achieved / pk["hbm_gbs"],
+                               "avg_launch_us": 1e3 * ph["fwd_ms"] / ph["fwd_launches"]}}
+
+    cpu = None
+    if not args.no_cpu and world == 1:
+        threads = max(1, min(os.cpu_count() or 1, 16))
+        nt_s, ns = 40, min(threads, wl.nshot)
+        v, secs = oracle_sample(wl, nt_s, ns, threads)
+        cpu = {"value": v, "unit": "GLL-point-updates/s", "cores": threads, "kind": "oracle",
+               "sample": f"{ns} shots x first {nt_s} steps of the {wl.nex}x{wl.nez} mesh, FP64 forward+adjoint+gradient ({secs:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLL-point-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{wl.name}, {wl.nshot} shots x {wl.nt} steps, {wl.nrec} receivers, "
+                               f"one shot per launch; UQ n={n}, k=50 pairs, p={p}, rank {rnk}",
+                   "nglob": N, "nt": wl.nt, "shots": wl.nshot, "tile": m.schedule,
+                   "l2": "inputs larger than L2 (36.7 GB forward history per shot)"},
+        "s_per_gradient": grad_ms / 1e3, "s_per_uq": uq_ms / 1e3,
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -205,6 +205,24 @@ int gbfwi_lowrank_invhess(gbfwi_bfgs *b, const float *X, int p, int rank,
 /* Free the store.  NULL is accepted. */
 int gbfwi_bfgs_destroy(gbfwi_bfgs *b);
 
+/* ------------------------------------------------------------ counters -- */
+
+/* Kernel launches issued through this library by the calling process since
+ * it was loaded (every entry point, every handle).  Host-only. */
+long long gbfwi_launch_count(void);
+
+/* Enable (1) or disable (0) per-phase timing of gbfwi_adjoint_gradient on
+ * this mesh: CUDA events recorded on the caller's stream around the forward
+ * passes and around the adjoint passes of every shot batch. */
+int gbfwi_enable_timing(gbfwi_mesh *mesh, int on);
+
+/* Device time (ms) of the forward passes and of the adjoint passes of the
+ * most recent timed gbfwi_adjoint_gradient on this mesh, and the number of
+ * time-step kernel launches in each (the adjoint passes include the segment
+ * recomputation when checkpointing).  -> EINVAL when nothing was timed. */
+int gbfwi_last_phase_times(const gbfwi_mesh *mesh, double *fwd_ms, double *adj_ms,
+                           long long *fwd_launches, long long *adj_launches);
+
 /* Static description of an error code. */
 const char *gbfwi_strerror(int code);
 

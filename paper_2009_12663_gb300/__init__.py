@@ -24,10 +24,15 @@ from ._lib import (ABI_SYMBOLS, GbfwiError, MeshDesc, Schedule, Source, check, l
 __all__ = [
     "Mesh", "Bfgs", "GbfwiError", "ABI_SYMBOLS", "mesh_create", "set_model", "forward",
     "adjoint_gradient", "precond_diag", "bfgs_create", "bfgs_update", "bfgs_apply",
-    "lowrank_invhess", "num_tiles", "tile_shape", "lib",
+    "lowrank_invhess", "num_tiles", "tile_shape", "lib", "launch_count",
 ]
 
 F32, F64, I32 = np.float32, np.float64, np.int32
+
+
+def launch_count() -> int:
+    """Kernel launches issued through the library by this process."""
+    return lib().gbfwi_launch_count()
 
 
 def num_tiles() -> int:
@@ -91,6 +96,16 @@ class Mesh:
     def set_schedule(self, shots_per_launch=1, tile=0, use_graph=0, ckpt_every=0):
         s = Schedule(int(shots_per_launch), int(tile), int(use_graph), int(ckpt_every))
         check(lib().gbfwi_set_schedule(self._h, ctypes.byref(s)), "set_schedule")
+
+    def enable_timing(self, on=True):
+        check(lib().gbfwi_enable_timing(self._h, int(bool(on))), "enable_timing")
+
+    def last_phase_times(self) -> dict:
+        f, a = ctypes.c_double(), ctypes.c_double()
+        nf, na = ctypes.c_longlong(), ctypes.c_longlong()
+        check(lib().gbfwi_last_phase_times(self._h, ctypes.byref(f), ctypes.byref(a), ctypes.byref(nf),
+                                           ctypes.byref(na)), "last_phase_times")
+        return dict(fwd_ms=f.value, adj_ms=a.value, fwd_launches=nf.value, adj_launches=na.value)
 
     def set_model(self, rho, vp, vs):
         check(lib().gbfwi_set_model(self._h, ptr(rho, F32), ptr(vp, F32), ptr(vs, F32),

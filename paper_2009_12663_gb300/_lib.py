@@ -28,7 +28,8 @@ ABI_SYMBOLS = (
     "gbfwi_num_tiles", "gbfwi_tile_shape", "gbfwi_get_schedule", "gbfwi_set_schedule",
     "gbfwi_set_model", "gbfwi_forward", "gbfwi_adjoint_gradient", "gbfwi_precond_diag",
     "gbfwi_bfgs_create", "gbfwi_bfgs_update", "gbfwi_bfgs_count", "gbfwi_bfgs_apply",
-    "gbfwi_lowrank_invhess", "gbfwi_bfgs_destroy", "gbfwi_strerror",
+    "gbfwi_lowrank_invhess", "gbfwi_bfgs_destroy", "gbfwi_launch_count", "gbfwi_enable_timing",
+    "gbfwi_last_phase_times", "gbfwi_strerror",
 )
 
 
@@ -90,6 +91,11 @@ def lib(path: str | None = None):
         L.gbfwi_lowrank_invhess.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
                                             ctypes.c_double, vp, vp, vp, vp]
         L.gbfwi_bfgs_destroy.argtypes = [vp]
+        L.gbfwi_launch_count.restype = ctypes.c_longlong
+        L.gbfwi_launch_count.argtypes = []
+        L.gbfwi_enable_timing.argtypes = [vp, ctypes.c_int]
+        L.gbfwi_last_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     return _LIB
 
 

@@ -451,10 +451,10 @@ int atb(gbfwi_bfgs *h, const float *A, long long lda, int ka, const float *Bm, l
     GB_TRY(h->part.ensure((size_t)nsplit * ka * kb * sizeof(double)));
     dim3 grid((unsigned)nsplit, (ka + AT - 1) / AT, (kb + AT - 1) / AT);
     atb_partial<<<grid, 256, 0, s>>>(A, lda, ka, Bm, ldb, kb, w, n, chunk, h->part.as<double>());
-    GB_CUDA(cudaGetLastError());
+    GB_LAUNCHED();
     int nab = ka * kb;
     atb_reduce<<<(nab + 255) / 256, 256, 0, s>>>(h->part.as<double>(), (int)nsplit, nab, out, ldo, kb);
-    GB_CUDA(cudaGetLastError());
+    GB_LAUNCHED();
     return GBFWI_OK;
 }
 
@@ -484,7 +484,7 @@ int combine(gbfwi_bfgs *h, const float *A1, const float *A2, int k1, int ktot, c
             combine_kernel<64><<<grid_n(n) / 2 + 1, 128, smem, s>>>(A1, A2, k1, ktot, n, coef, c0, cn, n, out, n, dw,
                                                                   Xc, n, beta);
         }
-        GB_CUDA(cudaGetLastError());
+        GB_LAUNCHED();
     }
     return GBFWI_OK;
 }
@@ -536,7 +536,7 @@ int apply_dev(gbfwi_bfgs *h, const float *Xd, int p, float *Zd, double gamma, in
     GB_TRY(atb(h, h->BY.as<float>(), n, k, Xd, n, p, nullptr, T + (long long)k * p, p, s));
     middle_kernel<<<(p + 63) / 64, 64, 0, s>>>(T, h->dSY.as<double>(), h->dYBY.as<double>(), k, h->kmax, p, gamma,
                                                scr, h->coef.as<float>());
-    GB_CUDA(cudaGetLastError());
+    GB_LAUNCHED();
     return combine(h, h->S.as<float>(), h->BY.as<float>(), k, 2 * k, h->coef.as<float>(), p, Zd,
                    h->B0.as<float>(), Xd, beta, s);
 }
@@ -597,7 +597,7 @@ extern "C" int gbfwi_bfgs_update(gbfwi_bfgs *h, const float *s_, const float *y_
     GB_CUDA(cudaMemcpyAsync(yk, y_, n * sizeof(float), gb_is_device_ptr(y_) ? cudaMemcpyDeviceToDevice
                                                                               : cudaMemcpyHostToDevice, s));
     mul_kernel<<<grid_n(n), 256, 0, s>>>(h->B0.as<float>(), yk, n, byk);
-    GB_CUDA(cudaGetLastError());
+    GB_LAUNCHED();
     // dots: s_i^T [y_k, s_k] (i <= k), (B0 y_i)^T y_k (i <= k), y_k^T y_k
     GB_TRY(reserve(h, 1, false));
     double *d1 = h->small.as<double>();          // [(k+1)][2]
@@ -662,7 +662,7 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
     } else {
         GB_TRY(h->X.ensure((size_t)p * n * sizeof(float)));
         philox_normal_kernel<<<grid_n((p * n + 3) / 4), 256, 0, s>>>(h->X.as<float>(), (long long)p * n, seed);
-        GB_CUDA(cudaGetLastError());
+        GB_LAUNCHED();
         Xd = h->X.as<float>();
     }
     GB_TRY(h->E.ensure((size_t)p * n * sizeof(float)));
@@ -687,17 +687,17 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
     GB_CUDA(cudaMemsetAsync(flag, 0, 16, s));
     GB_TRY(atb(h, E, n, p, E, n, p, nullptr, G, p, s));
     chol_kernel<<<1, 256, 0, s>>>(G, p, A, R1, Rinv, coef, flag);
-    GB_CUDA(cudaGetLastError());
+    GB_LAUNCHED();
     GB_TRY(combine(h, E, nullptr, p, p, coef, p, Q, nullptr, nullptr, 0.f, s));
     GB_TRY(atb(h, Q, n, p, Q, n, p, nullptr, G, p, s));
     chol_kernel<<<1, 256, 0, s>>>(G, p, A, R2, Rinv, coef, flag);
-    GB_CUDA(cudaGetLastError());
+    GB_LAUNCHED();
     GB_TRY(combine(h, Q, nullptr, p, p, coef, p, E, nullptr, nullptr, 0.f, s));   // final Q in E
     float *Qf = E;
     // 3. M1 = Q^T X ; Omega (Q^T X) = R2 R1 ; eigenpairs
     GB_TRY(atb(h, Qf, n, p, Xd, n, p, nullptr, M1, p, s));
     omega_eig_kernel<<<1, 256, 0, s>>>(R1, R2, M1, p, rank, work, lam, coef, flag, 60);
-    GB_CUDA(cudaGetLastError());
+    GB_LAUNCHED();
     // 4. V = Q U (first `rank` columns)
     const bool devV = V && gb_is_device_ptr(V);
     float *Vd = devV ? V : Q;     // Q buffer is free now
@@ -707,7 +707,7 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
         bool devS = gb_is_device_ptr(std_out);
         float *Sd = devS ? std_out : Qf;   // E buffer free after V
         std_kernel<<<grid_n(n), 256, 0, s>>>(Vd, lam, rank, h->B0.as<float>(), n, (float)eps_prior, Sd);
-        GB_CUDA(cudaGetLastError());
+        GB_LAUNCHED();
         if (!devS) GB_CUDA(cudaMemcpyAsync(std_out, Sd, n * sizeof(float), cudaMemcpyDeviceToHost, s));
     }
     if (V && !devV) GB_CUDA(cudaMemcpyAsync(V, Vd, (size_t)rank * n * sizeof(float), cudaMemcpyDeviceToHost, s));

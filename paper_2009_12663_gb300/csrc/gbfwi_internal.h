@@ -30,6 +30,14 @@
     } while (0)
 
 void gb_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+void gb_note_launch();
+
+// after every kernel launch: count it and surface launch errors
+#define GB_LAUNCHED()                 \
+    do {                              \
+        gb_note_launch();             \
+        GB_CUDA(cudaGetLastError());  \
+    } while (0)
 
 // ---------------------------------------------------------------------------
 // device buffers
@@ -116,6 +124,15 @@ struct gbfwi_mesh {
     DevBuf w_hist, w_vh, w_adj, w_wh, w_acc, w_snap, w_seis, w_sig, w_obs, w_grad,
         w_red, w_flag, w_shots, w_tmp, w_stage;
     DevBuf w_pc;        // preconditioner accumulators
+
+    // optional per-phase timing of adjoint_gradient
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;        // 4 per shot batch
+    int ev_used = 0;
+    long long fwd_launches = 0, adj_launches = 0;
+    bool timed_valid = false;
+    double fwd_ms = 0, adj_ms = 0;
+    ~gbfwi_mesh();
 };
 
 int gb_build_tile_lists(gbfwi_mesh *m, int tile);

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include "gbfwi_internal.h"
@@ -20,6 +21,34 @@ int gb_upload_gll(const double *D, const double *w);
 // ---------------------------------------------------------------------------
 
 static thread_local char g_err[512];
+static std::atomic<long long> g_launches{0};
+
+void gb_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" long long gbfwi_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+gbfwi_mesh::~gbfwi_mesh()
+{
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+}
+
+extern "C" int gbfwi_enable_timing(gbfwi_mesh *m, int on)
+{
+    if (!m || (on != 0 && on != 1)) return GBFWI_EINVAL;
+    m->timing = on != 0;
+    return GBFWI_OK;
+}
+
+extern "C" int gbfwi_last_phase_times(const gbfwi_mesh *m, double *fwd_ms, double *adj_ms,
+                                      long long *fwd_launches, long long *adj_launches)
+{
+    if (!m || !m->timed_valid) return GBFWI_EINVAL;
+    if (fwd_ms) *fwd_ms = m->fwd_ms;
+    if (adj_ms) *adj_ms = m->adj_ms;
+    if (fwd_launches) *fwd_launches = m->fwd_launches;
+    if (adj_launches) *adj_launches = m->adj_launches;
+    return GBFWI_OK;
+}
 
 void gb_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line)
 {
@@ -523,7 +552,7 @@ extern "C" int gbfwi_set_model(gbfwi_mesh *m, const float *rho, const float *vp,
     material_kernel<<<304, 256, 0, s>>>(m->d_model.as<float>(), m->d_wx.as<float>(), m->d_wz.as<float>(),
                                         m->d_bw.as<float4>(), m->nx, m->nz, m->pitch, (float)m->d.dt,
                                         m->d_lm.as<float2>(), m->d_minv.as<float>(), m->d_bnd.as<float4>());
-    GB_CUDA(cudaGetLastError());
+    GB_LAUNCHED();
     GB_CUDA(cudaStreamSynchronize(s));
     m->have_model = true;
     return GBFWI_OK;

@@ -546,36 +546,69 @@ extern "C" int gbfwi_adjoint_gradient(gbfwi_mesh *m, const int *shot_ids, int ns
     GB_CUDA(cudaMemsetAsync(flag, 0, 16, s));
     float *tot = m->w_grad.as<float>();
     GB_CUDA(cudaMemsetAsync(tot, 0, 5 * NP * sizeof(float), s));
+    const int nbatch = (nshot + Bmax - 1) / Bmax;
+    m->timed_valid = false;
+    if (m->timing) {
+        while ((int)m->ev.size() < 4 * nbatch) {
+            cudaEvent_t e;
+            GB_CUDA(cudaEventCreate(&e));
+            m->ev.push_back(e);
+        }
+        m->fwd_launches = m->adj_launches = 0;
+    }
+    auto mark = [&](int i) -> int {
+        if (m->timing) GB_CUDA(cudaEventRecord(m->ev[i], s));
+        return GBFWI_OK;
+    };
 
-    for (int i0 = 0; i0 < nshot; i0 += Bmax) {
+    for (int i0 = 0, bi = 0; i0 < nshot; i0 += Bmax, ++bi) {
         int B = std::min(Bmax, nshot - i0);
         Ctx c{m, &m->lists[tile], tile, B, s, m->w_shots.as<int>() + i0, NP};
         float *seis_d = m->w_seis.as<float>();
+        GB_TRY(mark(4 * bi));
         GB_TRY(forward_pass(c, h, seis_d));
+        GB_TRY(mark(4 * bi + 1));
+        m->fwd_launches += nt;
         // residual r = s - d (in place) and misfit 1/2 dt sum r^2
         long long nr = (long long)seis_shot * B;
         const int nblk = 1024;
         residual_kernel<<<nblk, 256, 0, s>>>(seis_d, (const float *)obs_d + seis_shot * i0, nr, partial, flag);
-        GB_CUDA(cudaGetLastError());
+        GB_LAUNCHED();
         misfit_finish<<<1, 32, 0, s>>>(partial, nblk, 0.5 * m->d.dt, mis_d);
-        GB_CUDA(cudaGetLastError());
+        GB_LAUNCHED();
         float *acc = m->w_acc.as<float>();
         GB_CUDA(cudaMemsetAsync(acc, 0, (size_t)B * 5 * NP * sizeof(float), s));
+        GB_TRY(mark(4 * bi + 2));
         GB_TRY(adjoint_pass(c, h, MODE_ADJ_G, seis_d, acc, 5 * NP, NP));
+        GB_TRY(mark(4 * bi + 3));
+        m->adj_launches += (h.C == 0) ? nt : 2LL * nt;
         acc_reduce<<<grid_for(5 * NP), 256, 0, s>>>(acc, B, 5, NP, tot);
-        GB_CUDA(cudaGetLastError());
+        GB_LAUNCHED();
     }
     const float dt = (float)m->d.dt;
     chain_kernel<<<grid_for(N), 256, 0, s>>>(tot, m->d_model.as<float>(), m->nx, m->nz, m->pitch, -dt * dt,
                                              grad_d);
-    GB_CUDA(cudaGetLastError());
+    GB_LAUNCHED();
     finite_check<<<grid_for(3 * N), 256, 0, s>>>(grad_d, 3 * N, flag);
-    GB_CUDA(cudaGetLastError());
+    GB_LAUNCHED();
     double mis_h = 0;
     int flag_h = 0;
     GB_CUDA(cudaMemcpyAsync(&mis_h, mis_d, sizeof(double), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaMemcpyAsync(&flag_h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
+    if (m->timing) {
+        double fm = 0, am = 0;
+        for (int bi = 0; bi < nbatch; ++bi) {
+            float a = 0, b = 0;
+            GB_CUDA(cudaEventElapsedTime(&a, m->ev[4 * bi], m->ev[4 * bi + 1]));
+            GB_CUDA(cudaEventElapsedTime(&b, m->ev[4 * bi + 2], m->ev[4 * bi + 3]));
+            fm += a;
+            am += b;
+        }
+        m->fwd_ms = fm;
+        m->adj_ms = am;
+        m->timed_valid = true;
+    }
     if (flag_h || !std::isfinite(mis_h)) return GBFWI_ENONFINITE;
     if (!dev_grad) {
         GB_CUDA(cudaMemcpyAsync(grad, grad_d, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -641,7 +674,7 @@ extern "C" int gbfwi_precond_diag(gbfwi_mesh *m, const int *shot_ids, int nshot,
             GB_TRY(adjoint_pass(c, h, MODE_ADJ_PC, seis_d, acc, 4 * NP, NP));
         }
         acc_reduce<<<grid_for(4 * NP), 256, 0, s>>>(acc, B, 4, NP, tot);
-        GB_CUDA(cudaGetLastError());
+        GB_LAUNCHED();
     }
     // time-integral factors: forward mode S0 = sum a.a (x dt), S1..3 = sum of
     // products of undivided differences (x 1/dt); receiver mode S0 = sum of
@@ -653,7 +686,7 @@ extern "C" int gbfwi_precond_diag(gbfwi_mesh *m, const int *shot_ids, int nshot,
     float *S1 = Hd + 3 * N, *S2 = Hd + 6 * N;
     precond_finish<<<grid_for(N), 256, 0, s>>>(tot, m->d_model.as<float>(), m->d_wx.as<float>(),
                                                m->d_wz.as<float>(), m->nx, m->nz, m->pitch, kind, f0, f1, Hd);
-    GB_CUDA(cudaGetLastError());
+    GB_LAUNCHED();
 
     // smoothing tables (node coordinates along each axis, 5-sigma index ranges)
     std::vector<float> cx(m->nx), cz(m->nz);
@@ -688,9 +721,9 @@ extern "C" int gbfwi_precond_diag(gbfwi_mesh *m, const int *shot_ids, int nshot,
     GB_CUDA(cudaMemcpyAsync(drz, rz.data(), m->nz * sizeof(int2), cudaMemcpyHostToDevice, s));
     float inv2s2 = (float)(1.0 / (2.0 * sigma * sigma));
     smooth_axis<<<grid_for(3 * N), 256, 0, s>>>(Hd, S1, m->nx, m->nz, 0, dcx, dwx, drx, inv2s2);
-    GB_CUDA(cudaGetLastError());
+    GB_LAUNCHED();
     smooth_axis<<<grid_for(3 * N), 256, 0, s>>>(S1, S2, m->nx, m->nz, 1, dcz, dwz, drz, inv2s2);
-    GB_CUDA(cudaGetLastError());
+    GB_LAUNCHED();
     // medians of the smoothed maps (rank (N-1)/2)
     GB_TRY(m->w_red.ensure((1024 + 8) * sizeof(double) + 4096));
     unsigned *rstate = (unsigned *)(m->w_red.as<char>() + (1024 + 8) * sizeof(double));
@@ -703,13 +736,13 @@ extern "C" int gbfwi_precond_diag(gbfwi_mesh *m, const int *shot_ids, int nshot,
             radix_hist<<<grid_for(N), 256, 0, s>>>(S2 + c * N, N, rstate, shift, rhist);
             radix_pick<<<1, 32, 0, s>>>(rstate, rhist, shift, med + c);
         }
-        GB_CUDA(cudaGetLastError());
+        GB_LAUNCHED();
     }
     const bool dev_b0 = gb_is_device_ptr(B0);
     GB_TRY(m->w_stage.ensure(m->w_stage.bytes));
     float *B0d = dev_b0 ? B0 : S1;   // S1 is free after the second pass
     b0_kernel<<<grid_for(3 * N), 256, 0, s>>>(S2, med, N, (float)damp, B0d);
-    GB_CUDA(cudaGetLastError());
+    GB_LAUNCHED();
     if (!dev_b0) GB_CUDA(cudaMemcpyAsync(B0, B0d, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s));
     if (H) {
         if (gb_is_device_ptr(H))

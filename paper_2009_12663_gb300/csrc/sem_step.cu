@@ -78,7 +78,7 @@ __device__ __forceinline__ void grad_at(const float (&px)[25], const float (&pz)
 // element nodal forces (K u restricted to one element) -> out[25]
 template <int NWXP>
 __device__ __forceinline__ void element_force(const float2 *__restrict__ sw, const float2 *__restrict__ slm,
-                                              int base, float2 *__restrict__ out)
+                                              int base, float2 (&out)[25])
 {
     float px[25], pz[25];
     load_patch<NWXP>(sw, base, px, pz);
@@ -121,7 +121,7 @@ __device__ __forceinline__ void element_force(const float2 *__restrict__ sw, con
 //   NC == 3 (preconditioner): [div A div B, exx exx' + ezz ezz', gam gam']
 template <int NWXP, int NC>
 __device__ __forceinline__ void element_products(const float2 *__restrict__ wa, const float2 *__restrict__ wb,
-                                                 int base, float *__restrict__ out)
+                                                 int base, float (&out)[25 * NC])
 {
     float ax[25], az[25], bx[25], bz[25];
     load_patch<NWXP>(wa, base, ax, az);
@@ -150,7 +150,7 @@ __device__ __forceinline__ void element_products(const float2 *__restrict__ wa, 
 
 // same as above with A == B (forward preconditioner: squares)
 template <int NWXP>
-__device__ __forceinline__ void element_squares(const float2 *__restrict__ wa, int base, float *__restrict__ out)
+__device__ __forceinline__ void element_squares(const float2 *__restrict__ wa, int base, float (&out)[75])
 {
     float ax[25], az[25];
     load_patch<NWXP>(wa, base, ax, az);
@@ -200,40 +200,124 @@ __device__ __forceinline__ void load_window(float2 *__restrict__ dst, const floa
 
 }  // namespace
 
-template <int TX, int TZ, int MODE>
-__global__ void __launch_bounds__((TX + 1) * (TZ + 1), 1) sem_step_kernel(const StepArgs a)
+// ---------------------------------------------------------------------------
+// asynchronous global -> shared copies (16 B, zero-filled beyond src_bytes)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes)
 {
-    constexpr int NE = (TX + 1) * (TZ + 1);
-    constexpr int NT = NE;
-    constexpr int NWZ = 4 * TZ + 5, NWXP = 4 * TX + 6;
-    constexpr int OX = 4 * TX + 1, OZ = 4 * TZ + 1;
-    constexpr int NC = (MODE == MODE_ADJ_G) ? 2 : ((MODE == MODE_FWD) ? 2 : 3);
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+
+// window of a float2 node field: rows iz0.., node pairs from ix0 (even)
+template <int NWZ, int NWXP, int NT>
+__device__ __forceinline__ void prefetch_window(float2 *dst, const float2 *src, int ix0, int iz0, int nz, int pitch)
+{
+    constexpr int NP = NWXP / 2;
+    for (int q = threadIdx.x; q < NWZ * NP; q += NT) {
+        int r = q / NP, p = q - r * NP;
+        int iz = iz0 + r, ix = ix0 + 2 * p;
+        bool in = (iz >= 0) && (iz < nz) && (ix >= 0) && (ix < pitch);
+        const float2 *g = in ? src + (long long)iz * pitch + ix : src;
+        cp_async16(dst + r * NWXP + 2 * p, g, in ? 16 : 0);
+    }
+}
+
+// owned box of a float2 field: oh rows of ow nodes from (ixo, izo); smem row pitch OXP (even)
+template <int OXP, int NT>
+__device__ __forceinline__ void prefetch_owned2(float2 *dst, const float2 *src, int ixo, int izo, int ow, int oh,
+                                                int pitch)
+{
+    const int np = (ow + 1) >> 1;
+    for (int q = threadIdx.x; q < oh * np; q += NT) {
+        int r = q / np, p = q - r * np;
+        cp_async16(dst + r * OXP + 2 * p, src + (long long)(izo + r) * pitch + ixo + 2 * p, 16);
+    }
+}
+
+// owned box of a float field; smem row pitch OXQ (multiple of 4)
+template <int OXQ, int NT>
+__device__ __forceinline__ void prefetch_owned1(float *dst, const float *src, int ixo, int izo, int ow, int oh,
+                                                int pitch)
+{
+    const int nq = (ow + 3) >> 2;
+    for (int q = threadIdx.x; q < oh * nq; q += NT) {
+        int r = q / nq, p = q - r * nq;
+        int ix = ixo + 4 * p;
+        int bytes = max(0, min(16, (pitch - ix) * 4));
+        cp_async16(dst + r * OXQ + 4 * p, src + (long long)(izo + r) * pitch + ix, bytes);
+    }
+}
+
+template <int TX, int TZ, int MODE>
+struct StepShape {
+    static constexpr int NT = (TX + 1) * (TZ + 1);          // one thread per element of the extended tile
+    static constexpr int NWZ = 4 * TZ + 5, NWXP = 4 * TX + 6;
+    static constexpr int WIN = NWZ * NWXP;                    // float2 per window
+    static constexpr int OX = 4 * TX + 1, OZ = 4 * TZ + 1;   // largest owned box
+    static constexpr int OXP = 4 * TX + 2;                    // float2 row pitch of owned boxes
+    static constexpr int OXQ = 4 * TX + 4;                    // float row pitch of owned boxes
+    static constexpr int CW = OX <= 32 ? 32 : (OX <= 64 ? 64 : 128);   // owned-node columns per pass
+    static constexpr int RPP = NT / CW;                       // owned-node rows per pass
+    static constexpr int NC = (MODE == MODE_FWD_PC || MODE == MODE_ADJ_PC) ? 3 : 2;
+    static constexpr int NWIN = (MODE == MODE_ADJ_G) ? 4 : 3;  // u, lambda-mu, node sums (+ history)
+    static constexpr int NACC = (MODE == MODE_ADJ_G) ? 3 : 0;  // accumulators staged in shared memory
+    static constexpr int WIN4 = (NC == 3) ? (WIN + 3) / 4 * 4 : 0;  // 3rd node-sum plane (floats)
+    static constexpr int MINB = ((MODE == MODE_FWD ? 384 : 256) / NT) > 0 ? (MODE == MODE_FWD ? 384 : 256) / NT : 1;
+    static constexpr size_t bytes = (size_t)NWIN * WIN * sizeof(float2) + (size_t)WIN4 * sizeof(float) +
+                                    (size_t)OZ * OXP * sizeof(float2) + (size_t)(1 + NACC) * OZ * OXQ * sizeof(float);
+    static_assert(NT % CW == 0 && CW >= OX, "owned-node mapping");
+};
+
+template <int TX, int TZ, int MODE>
+__global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ, MODE>::MINB)
+    sem_step_kernel(const StepArgs a)
+{
+    using S = StepShape<TX, TZ, MODE>;
+    constexpr int NT = S::NT, NWXP = S::NWXP, NWZ = S::NWZ, WIN = S::WIN;
+    constexpr int OXP = S::OXP, OXQ = S::OXQ, CW = S::CW, RPP = S::RPP, NC = S::NC;
 
     extern __shared__ float4 smem4[];
-    float2 *sw = reinterpret_cast<float2 *>(smem4);      // field window [NWZ][NWXP]
-    float2 *slm = sw + NWZ * NWXP;                         // (lambda, mu) window; later 2nd field
-    float *sfl = reinterpret_cast<float *>(slm + NWZ * NWXP);   // element results [NE][25][NC]
-    float2 *sF = reinterpret_cast<float2 *>(sfl + NE * 25 * NC); // source forces [OZ][OX]
+    float2 *sw = reinterpret_cast<float2 *>(smem4);     // field window (u_{n+1} or w_{j+1})
+    float2 *slm = sw + WIN;                              // (lambda, mu) window; 2nd field in P-modes
+    float2 *sK = slm + WIN;                              // node sums over the window
+    float2 *su2 = sK + WIN;                              // forward-history window (MODE_ADJ_G)
+    float *sK3 = reinterpret_cast<float *>(sw + S::NWIN * WIN);   // 3rd node sum (NC == 3)
+    float2 *svh = reinterpret_cast<float2 *>(sK3 + S::WIN4);       // owned half-step velocity
+    float *sminv = reinterpret_cast<float *>(svh + S::OZ * OXP);
+    float *sacc = sminv + S::OZ * OXQ;                   // [NACC][OZ][OXQ]
 
     const int b = blockIdx.z;
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
     const int ex0 = blockIdx.x * TX, ez0 = blockIdx.y * TZ;
     const int ix0 = 4 * ex0 - 4, iz0 = 4 * ez0 - 4;
+    const int ixo = 4 * ex0, izo = 4 * ez0;              // owned box origin
     const int pitch = a.pitch;
-    const long long fo = (long long)b * a.fstride;   // shots of a field are fstride apart
-
-    // owned node box
+    const long long fo = (long long)b * a.fstride;
     const int ixe = (ex0 + TX >= a.nex) ? a.nx : 4 * (ex0 + TX);
     const int ize = (ez0 + TZ >= a.nez) ? a.nz : 4 * (ez0 + TZ);
-    const int ow = ixe - 4 * ex0, oh = ize - 4 * ez0;
+    const int ow = ixe - ixo, oh = ize - izo;
 
-    // ---- phase 0: windows, zero source forces
-    for (int q = threadIdx.x; q < OX * OZ; q += NT) sF[q] = make_float2(0.f, 0.f);
-    load_window<NWZ, NWXP, NT>(sw, a.ucur + fo, nullptr, 0, ix0, iz0, a.nz, pitch);
-    load_window<NWZ, NWXP, NT>(slm, a.lm, nullptr, 0, ix0, iz0, a.nz, pitch);
+    // ---- phase 0: asynchronous prefetch of every input of this step
+    prefetch_window<NWZ, NWXP, NT>(sw, a.ucur + fo, ix0, iz0, a.nz, pitch);
+    prefetch_window<NWZ, NWXP, NT>(slm, a.lm, ix0, iz0, a.nz, pitch);
+    if (MODE == MODE_ADJ_G)
+        prefetch_window<NWZ, NWXP, NT>(su2, a.h0 + (long long)b * a.hstride, ix0, iz0, a.nz, pitch);
+    prefetch_owned2<OXP, NT>(svh, a.vh + fo, ixo, izo, ow, oh, pitch);
+    prefetch_owned1<OXQ, NT>(sminv, a.minv, ixo, izo, ow, oh, pitch);
+    if (MODE == MODE_ADJ_G) {
+        const float *ab = a.acc + (long long)b * a.acc_shot_stride;
+        for (int c = 0; c < 3; ++c)
+            prefetch_owned1<OXQ, NT>(sacc + c * S::OZ * OXQ, ab + c * a.acc_comp_stride, ixo, izo, ow, oh, pitch);
+    }
+    for (int q = threadIdx.x; q < WIN; q += NT) sK[q] = make_float2(0.f, 0.f);
+    cp_async_wait_all();
     __syncthreads();
 
-    // ---- phase 1: records, element forces, source forces
+    // ---- phase 1: records, element forces accumulated by colour, sources
     if (MODE == MODE_FWD || MODE == MODE_FWD_PC) {
         if (a.seis) {
             int rb = a.rec_tptr[tile], re = a.rec_tptr[tile + 1];
@@ -254,13 +338,28 @@ __global__ void __launch_bounds__((TX + 1) * (TZ + 1), 1) sem_step_kernel(const 
             }
         }
     }
+    const int e = threadIdx.x;
+    const int elx = e % (TX + 1), elz = e / (TX + 1);
+    const bool evalid = (ex0 - 1 + elx >= 0) && (ez0 - 1 + elz >= 0) && (ex0 - 1 + elx < a.nex) &&
+                        (ez0 - 1 + elz < a.nez);
+    const int ebase = 4 * elz * NWXP + 4 * elx;
+    const int colour = (elx & 1) | ((elz & 1) << 1);
     {
-        int e = threadIdx.x;          // one element per thread
-        int elx = e % (TX + 1), elz = e / (TX + 1);
-        int ex = ex0 - 1 + elx, ez = ez0 - 1 + elz;
-        if (ex >= 0 && ez >= 0 && ex < a.nex && ez < a.nez) {
-            int base = 4 * elz * NWXP + 4 * elx;
-            element_force<NWXP>(sw, slm, base, reinterpret_cast<float2 *>(sfl) + e * 25);
+        float2 f[25];
+        if (evalid) element_force<NWXP>(sw, slm, ebase, f);
+#pragma unroll 1
+        for (int pass = 0; pass < 4; ++pass) {
+            if (evalid && colour == pass) {
+#pragma unroll
+                for (int j = 0; j < 5; ++j)
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) {
+                        float2 &k = sK[ebase + j * NWXP + i];
+                        k.x += f[j * 5 + i].x;
+                        k.y += f[j * 5 + i].y;
+                    }
+            }
+            __syncthreads();
         }
     }
     {
@@ -276,68 +375,49 @@ __global__ void __launch_bounds__((TX + 1) * (TZ + 1), 1) sem_step_kernel(const 
                 fx = fmaf(E.wx, sig[(long long)E.cx * a.sig_chan_stride], fx);
                 fz = fmaf(E.wz, sig[(long long)E.cz * a.sig_chan_stride], fz);
             }
-            sF[G.node] = make_float2(fx * a.sig_scale, fz * a.sig_scale);
+            int oz = G.node / S::OX, ox = G.node - oz * S::OX;
+            float2 &k = sK[(oz + 4) * NWXP + ox + 4];      // K u - F
+            k.x -= fx * a.sig_scale;
+            k.y -= fz * a.sig_scale;
         }
     }
     __syncthreads();
 
-    // ---- phase 2: gather K u, Newmark update, pointwise accumulations
+    // ---- phase 2: Newmark update of the owned nodes, pointwise accumulations
     const float dt = a.dt;
-    const float2 *sf2 = reinterpret_cast<const float2 *>(sfl);
-    for (int q = threadIdx.x; q < ow * oh; q += NT) {
-        int oz = q / ow, ox = q - oz * ow;
-        int ix = 4 * ex0 + ox, iz = 4 * ez0 + oz;
-        int wxi = ox + 4, wzi = oz + 4;
-        int elx1 = wxi >> 2, li1 = wxi & 3;
-        int elz1 = wzi >> 2, lj1 = wzi & 3;
-        float kx = 0.f, kz = 0.f;
-#pragma unroll
-        for (int cz = 0; cz < 2; ++cz) {
-            int elz = cz == 0 ? elz1 - 1 : elz1, lj = cz == 0 ? 4 : lj1;
-            if (cz == 0 && lj1 != 0) continue;
-            int ez = ez0 - 1 + elz;
-            if (ez < 0 || ez >= a.nez) continue;
-#pragma unroll
-            for (int cx = 0; cx < 2; ++cx) {
-                int elx = cx == 0 ? elx1 - 1 : elx1, li = cx == 0 ? 4 : li1;
-                if (cx == 0 && li1 != 0) continue;
-                int ex = ex0 - 1 + elx;
-                if (ex < 0 || ex >= a.nex) continue;
-                float2 f = sf2[(elz * (TX + 1) + elx) * 25 + lj * 5 + li];
-                kx += f.x;
-                kz += f.y;
-            }
-        }
-        float2 F = sF[oz * OX + ox];
-        long long g = (long long)iz * pitch + ix;
-        float2 v = a.vh[fo + g];
-        bool edge = (ix == 0) | (ix == a.nx - 1) | (iz == 0) | (iz == a.nz - 1);
+    const int ox = threadIdx.x % CW;
+    for (int oz = threadIdx.x / CW; oz < oh; oz += RPP) {
+        if (ox >= ow) continue;
+        const int ix = ixo + ox, iz = izo + oz;
+        const int wq = (oz + 4) * NWXP + ox + 4;
+        const long long g = (long long)iz * pitch + ix;
+        float2 k = sK[wq];
+        float2 v = svh[oz * OXP + ox];
+        const bool edge = (ix == 0) | (ix == a.nx - 1) | (iz == 0) | (iz == a.nz - 1);
         float ax, az;
         if (edge) {
             float4 bd = a.bnd[g];
-            ax = (F.x - kx - bd.x * v.x) * bd.z;
-            az = (F.y - kz - bd.y * v.y) * bd.w;
+            ax = -(k.x + bd.x * v.x) * bd.z;
+            az = -(k.y + bd.y * v.y) * bd.w;
         } else {
-            float mi = a.minv[g];
-            ax = (F.x - kx) * mi;
-            az = (F.y - kz) * mi;
+            float mi = sminv[oz * OXQ + ox];
+            ax = -k.x * mi;
+            az = -k.y * mi;
         }
         float2 vn = make_float2(fmaf(dt, ax, v.x), fmaf(dt, az, v.y));
-        float2 uc = sw[wzi * NWXP + wxi];
+        float2 uc = sw[wq];
         a.vh[fo + g] = vn;
         a.unext[fo + g] = make_float2(fmaf(dt, vn.x, uc.x), fmaf(dt, vn.y, uc.y));
-
         if (MODE == MODE_FWD_PC) {
             float *acc = a.acc + (long long)b * a.acc_shot_stride + g;
             acc[0] += fmaf(ax, ax, az * az);
         } else if (MODE == MODE_ADJ_G) {
-            const long long ho = (long long)b * a.hstride;
-            float2 uk = a.h0[ho + g];
-            float *acc = a.acc + (long long)b * a.acc_shot_stride + g;
-            const long long cs = a.acc_comp_stride;
+            float2 uk = su2[wq];
             float wsum = a.wxs[ix] * a.wzs[iz];
-            acc[2 * cs] += wsum * fmaf(uk.x, ax, uk.y * az);
+            sacc[2 * S::OZ * OXQ + oz * OXQ + ox] += wsum * fmaf(uk.x, ax, uk.y * az);
             if (edge) {
+                float *acc = a.acc + (long long)b * a.acc_shot_stride + g;
+                const long long cs = a.acc_comp_stride;
                 float4 w4 = a.bw[g];
                 float vx = 0.5f * (v.x + vn.x), vz = 0.5f * (v.y + vn.y);
                 acc[3 * cs] += fmaf(w4.x * uk.x, vx, w4.y * uk.y * vz);
@@ -352,91 +432,87 @@ __global__ void __launch_bounds__((TX + 1) * (TZ + 1), 1) sem_step_kernel(const 
             acc[0] += fmaf(fxa, ax, fza * az);
         }
     }
-    if (MODE == MODE_FWD) return;
+    if constexpr (MODE == MODE_FWD) return;
     __syncthreads();
 
-    // ---- phase 3: second windows
+    // ---- phase 3: second windows (P-modes) and cleared node sums
     if (MODE == MODE_FWD_PC) {
-        // sw <- u_{n+1} - u_n
-        load_window<NWZ, NWXP, NT>(sw, a.uold + fo, nullptr, 1, ix0, iz0, a.nz, pitch);
-    } else if (MODE == MODE_ADJ_G) {
+        load_window<NWZ, NWXP, NT>(sw, a.uold + fo, nullptr, 1, ix0, iz0, a.nz, pitch);      // u_{n+1} - u_n
+    } else if (MODE == MODE_ADJ_PC) {
         const long long ho = (long long)b * a.hstride;
-        load_window<NWZ, NWXP, NT>(slm, a.h0 + ho, nullptr, 0, ix0, iz0, a.nz, pitch);
-    } else {
-        const long long ho = (long long)b * a.hstride;
-        load_window<NWZ, NWXP, NT>(slm, a.h0 + ho, a.h1 + ho, 2, ix0, iz0, a.nz, pitch);
-        load_window<NWZ, NWXP, NT>(sw, a.uold + fo, nullptr, 1, ix0, iz0, a.nz, pitch);
+        load_window<NWZ, NWXP, NT>(slm, a.h0 + ho, a.h1 + ho, 2, ix0, iz0, a.nz, pitch);     // u_{k+1} - u_k
+        load_window<NWZ, NWXP, NT>(sw, a.uold + fo, nullptr, 1, ix0, iz0, a.nz, pitch);      // w_{j+1} - w_j
+    }
+    for (int q = threadIdx.x; q < WIN; q += NT) {
+        sK[q] = make_float2(0.f, 0.f);
+        if (NC == 3) sK3[q] = 0.f;
     }
     __syncthreads();
 
-    // ---- phase 4: element products
+    // ---- phase 4: element products accumulated by colour
     {
-        int e = threadIdx.x;
-        int elx = e % (TX + 1), elz = e / (TX + 1);
-        int ex = ex0 - 1 + elx, ez = ez0 - 1 + elz;
-        if (ex >= 0 && ez >= 0 && ex < a.nex && ez < a.nez) {
-            int base = 4 * elz * NWXP + 4 * elx;
-            if (MODE == MODE_FWD_PC)
-                element_squares<NWXP>(sw, base, sfl + e * 25 * NC);
+        float pr[25 * NC];
+        if (evalid) {
+            if constexpr (MODE == MODE_FWD_PC)
+                element_squares<NWXP>(sw, ebase, pr);
+            else if constexpr (MODE == MODE_ADJ_G)
+                element_products<NWXP, NC>(sw, su2, ebase, pr);
             else
-                element_products<NWXP, NC>(sw, slm, base, sfl + e * 25 * NC);
+                element_products<NWXP, NC>(sw, slm, ebase, pr);
+        }
+#pragma unroll 1
+        for (int pass = 0; pass < 4; ++pass) {
+            if (evalid && colour == pass) {
+#pragma unroll
+                for (int j = 0; j < 5; ++j)
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) {
+                        int q = ebase + j * NWXP + i, l = (j * 5 + i) * NC;
+                        float2 &k = sK[q];
+                        k.x += pr[l];
+                        k.y += pr[l + 1];
+                        if (NC == 3) sK3[q] += pr[l + 2];
+                    }
+            }
+            __syncthreads();
         }
     }
-    __syncthreads();
 
-    // ---- phase 5: gather products into the accumulators
-    const int c0 = (MODE == MODE_ADJ_G) ? 0 : 1;
-    for (int q = threadIdx.x; q < ow * oh; q += NT) {
-        int oz = q / ow, ox = q - oz * ow;
-        int ix = 4 * ex0 + ox, iz = 4 * ez0 + oz;
-        int wxi = ox + 4, wzi = oz + 4;
-        int elx1 = wxi >> 2, li1 = wxi & 3;
-        int elz1 = wzi >> 2, lj1 = wzi & 3;
-        float s[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) s[c] = 0.f;
-#pragma unroll
-        for (int cz = 0; cz < 2; ++cz) {
-            int elz = cz == 0 ? elz1 - 1 : elz1, lj = cz == 0 ? 4 : lj1;
-            if (cz == 0 && lj1 != 0) continue;
-            int ez = ez0 - 1 + elz;
-            if (ez < 0 || ez >= a.nez) continue;
-#pragma unroll
-            for (int cx = 0; cx < 2; ++cx) {
-                int elx = cx == 0 ? elx1 - 1 : elx1, li = cx == 0 ? 4 : li1;
-                if (cx == 0 && li1 != 0) continue;
-                int ex = ex0 - 1 + elx;
-                if (ex < 0 || ex >= a.nex) continue;
-                const float *p = sfl + ((elz * (TX + 1) + elx) * 25 + lj * 5 + li) * NC;
-#pragma unroll
-                for (int c = 0; c < NC; ++c) s[c] += p[c];
-            }
-        }
-        long long g = (long long)iz * pitch + ix;
+    // ---- phase 5: accumulate into the global sums
+    for (int oz = threadIdx.x / CW; oz < oh; oz += RPP) {
+        if (ox >= ow) continue;
+        const int ix = ixo + ox, iz = izo + oz;
+        const int wq = (oz + 4) * NWXP + ox + 4;
+        const long long g = (long long)iz * pitch + ix;
+        float2 k = sK[wq];
         float *acc = a.acc + (long long)b * a.acc_shot_stride + g;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) acc[(c0 + c) * a.acc_comp_stride] += s[c];
+        const long long cs = a.acc_comp_stride;
+        if (MODE == MODE_ADJ_G) {
+            const int so = oz * OXQ + ox;
+            acc[0] = sacc[so] + k.x;
+            acc[cs] = sacc[S::OZ * OXQ + so] + k.y;
+            acc[2 * cs] = sacc[2 * S::OZ * OXQ + so];
+        } else {
+            acc[cs] += k.x;
+            acc[2 * cs] += k.y;
+            acc[3 * cs] += sK3[wq];
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
 
-template <int TX, int TZ>
-static size_t step_smem(int mode)
+template <int TX, int TZ, int MODE>
+static size_t step_smem()
 {
-    constexpr int NE = (TX + 1) * (TZ + 1);
-    constexpr int NWZ = 4 * TZ + 5, NWXP = 4 * TX + 6;
-    constexpr int OX = 4 * TX + 1, OZ = 4 * TZ + 1;
-    int NC = (mode == MODE_FWD || mode == MODE_ADJ_G) ? 2 : 3;
-    return (size_t)2 * NWZ * NWXP * sizeof(float2) + (size_t)NE * 25 * NC * sizeof(float) +
-           (size_t)OX * OZ * sizeof(float2);
+    return StepShape<TX, TZ, MODE>::bytes;
 }
 
 template <int TX, int TZ, int MODE>
 static int launch_one(const StepArgs &a, int nbatch, cudaStream_t s)
 {
     constexpr int NE = (TX + 1) * (TZ + 1);
-    size_t smem = step_smem<TX, TZ>(MODE);
+    size_t smem = step_smem<TX, TZ, MODE>();
     static bool attr_done[64] = {};          // per device ordinal
     int dev = 0;
     cudaGetDevice(&dev);
@@ -447,7 +523,7 @@ static int launch_one(const StepArgs &a, int nbatch, cudaStream_t s)
     }
     dim3 grid((a.nex + TX - 1) / TX, (a.nez + TZ - 1) / TZ, nbatch);
     sem_step_kernel<TX, TZ, MODE><<<grid, NE, smem, s>>>(a);
-    GB_CUDA(cudaGetLastError());
+    GB_LAUNCHED();
     return GBFWI_OK;
 }
 
