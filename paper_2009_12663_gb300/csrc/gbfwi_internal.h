@@ -91,7 +91,7 @@ struct TileLists {
 
 struct gbfwi_mesh {
     gbfwi_mesh_desc d{};
-    int nx = 0, nz = 0, pitch = 0;      // node grid; pitch = row length in nodes (even)
+    int nx = 0, nz = 0, pitch = 0;      // node grid; pitch = row length in nodes (multiple of 4)
     double xi[GB_NG], w[GB_NG], D[GB_NG][GB_NG];
     std::vector<gbfwi_source> src;
     std::vector<double> rec_xz;

@@ -186,7 +186,10 @@ extern "C" int gbfwi_mesh_create(const gbfwi_mesh_desc *desc, const gbfwi_source
     m->d = d;
     m->nx = 4 * d.nex + 1;
     m->nz = 4 * d.nez + 1;
-    m->pitch = (m->nx + 1) & ~1;
+    // row pitch: a multiple of 4 nodes, so every row of every node field
+    // (float, float2, float4) starts on a 16-byte boundary, as the 16-byte
+    // asynchronous copies of the step kernel require
+    m->pitch = (m->nx + 3) & ~3;
     double c[5][5];
     gll5(m->xi, m->w);
     lagrange_coeffs(m->xi, c);

@@ -343,7 +343,9 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
     const bool evalid = (ex0 - 1 + elx >= 0) && (ez0 - 1 + elz >= 0) && (ex0 - 1 + elx < a.nex) &&
                         (ez0 - 1 + elz < a.nez);
     const int ebase = 4 * elz * NWXP + 4 * elx;
-    const int colour = (elx & 1) | ((elz & 1) << 1);
+    // colour by global element parity: every node then sums its element
+    // contributions in the same order whatever the tile shape
+    const int colour = ((ex0 - 1 + elx) & 1) | (((ez0 - 1 + elz) & 1) << 1);
     {
         float2 f[25];
         if (evalid) element_force<NWXP>(sw, slm, ebase, f);
@@ -543,6 +545,11 @@ const TileShape kTiles[kNumTiles] = {{15, 7}, {7, 15}, {7, 7}, {15, 15}, {31, 3}
 
 int gb_launch_step(int mode, int tile, const StepArgs &a, int nbatch, cudaStream_t s)
 {
+    // 16-byte copies need 16-byte aligned rows and field bases
+    if (a.pitch % 4 != 0 || a.fstride % 2 != 0 || a.hstride % 2 != 0 || a.acc_comp_stride % 4 != 0 ||
+        a.acc_shot_stride % 4 != 0 || ((uintptr_t)a.ucur & 15) || ((uintptr_t)a.vh & 15) ||
+        ((uintptr_t)a.minv & 15) || ((uintptr_t)a.acc & 15) || ((uintptr_t)a.h0 & 15))
+        return GBFWI_EINVAL;
     switch (tile) {
     case 0: return launch_mode<15, 7>(mode, a, nbatch, s);
     case 1: return launch_mode<7, 15>(mode, a, nbatch, s);
