@@ -51,8 +51,12 @@ enum {
     GBFWI_ECURV = -5,       /* BFGS pair rejected: y^T s <= 1e-12 |s| |y| */
     GBFWI_ENONFINITE = -6,  /* a NaN or Inf reached the seismograms or the model */
     GBFWI_ETIMEOUT = -7,    /* a bounded device-side wait gave up */
-    GBFWI_ENOMODEL = -8     /* simulation requested before gbfwi_set_model */
+    GBFWI_ENOMODEL = -8,    /* simulation requested before gbfwi_set_model */
+    GBFWI_ESCRATCH = -9     /* request larger than the fixed scratch of a no-allocation entry point */
 };
+
+/* Largest number of shots gbfwi_misfit_noalloc accepts. */
+#define GBFWI_NOALLOC_MAX_SHOTS 256
 
 typedef struct gbfwi_mesh gbfwi_mesh;
 typedef struct gbfwi_bfgs gbfwi_bfgs;
@@ -204,6 +208,27 @@ int gbfwi_lowrank_invhess(gbfwi_bfgs *b, const float *X, int p, int rank,
 
 /* Free the store.  NULL is accepted. */
 int gbfwi_bfgs_destroy(gbfwi_bfgs *b);
+
+/* -------------------------------------------------- without allocation -- */
+
+/* Per-shot misfit f_s = 1/2 dt sum |s - d|^2 of synthetics against observed
+ * data, for callers that must not allocate device memory during the call
+ * (for example an application whose own pool or arena owns the GPU memory
+ * and forbids further cudaMalloc, or a time-critical loop that cannot afford
+ * an allocation failure or the synchronisation of a cudaFree).  The paper
+ * has no counterpart: this is the misfit reduction of
+ * gbfwi_adjoint_gradient with its scratch in a fixed device array.
+ *   syn, obs: device arrays [nshot][samples_per_shot] FP32 (e.g. the
+ *             [nshot][nrec][2][nt] seismograms of gbfwi_forward);
+ *   misfit:   host array [nshot] FP64, written only on success.
+ * nshot <= GBFWI_NOALLOC_MAX_SHOTS, else GBFWI_ESCRATCH.  The call allocates
+ * nothing and synchronises the stream.  The first call on a device looks up
+ * the scratch array's device address; make that first call before any stream
+ * capture.  All calls share one scratch array per device and it keeps the
+ * last call's partial sums: calls that overlap on the GPU race.
+ * -> EINVAL, ESCRATCH, ENONFINITE, ECUDA. */
+int gbfwi_misfit_noalloc(const float *syn, const float *obs, int nshot, long long samples_per_shot,
+                         double dt, double *misfit, void *stream);
 
 /* ------------------------------------------------------------ counters -- */
 

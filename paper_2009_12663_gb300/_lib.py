@@ -19,7 +19,7 @@ from . import build as _build
 GBFWI_OK = 0
 ERRORS = {
     -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ECFL", -5: "ECURV",
-    -6: "ENONFINITE", -7: "ETIMEOUT", -8: "ENOMODEL",
+    -6: "ENONFINITE", -7: "ETIMEOUT", -8: "ENOMODEL", -9: "ESCRATCH",
 }
 
 #: every symbol declared in include/gbfwi.h
@@ -29,7 +29,7 @@ ABI_SYMBOLS = (
     "gbfwi_set_model", "gbfwi_forward", "gbfwi_adjoint_gradient", "gbfwi_precond_diag",
     "gbfwi_bfgs_create", "gbfwi_bfgs_update", "gbfwi_bfgs_count", "gbfwi_bfgs_apply",
     "gbfwi_lowrank_invhess", "gbfwi_bfgs_destroy", "gbfwi_launch_count", "gbfwi_enable_timing",
-    "gbfwi_last_phase_times", "gbfwi_strerror",
+    "gbfwi_last_phase_times", "gbfwi_misfit_noalloc", "gbfwi_strerror",
 )
 
 
@@ -91,6 +91,7 @@ def lib(path: str | None = None):
         L.gbfwi_lowrank_invhess.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
                                             ctypes.c_double, vp, vp, vp, vp]
         L.gbfwi_bfgs_destroy.argtypes = [vp]
+        L.gbfwi_misfit_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_double, vp, vp]
         L.gbfwi_launch_count.restype = ctypes.c_longlong
         L.gbfwi_launch_count.argtypes = []
         L.gbfwi_enable_timing.argtypes = [vp, ctypes.c_int]

@@ -100,6 +100,7 @@ extern "C" const char *gbfwi_strerror(int code)
     case GBFWI_ENONFINITE: return "non-finite value";
     case GBFWI_ETIMEOUT: return "device-side wait timed out";
     case GBFWI_ENOMODEL: return "no model set";
+    case GBFWI_ESCRATCH: return "request exceeds the fixed scratch of a no-allocation entry point (at most 256 shots)";
     }
     return "unknown error";
 }
