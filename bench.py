@@ -119,17 +119,21 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_record(kernel: str):
-    """DRAM traffic of `kernel` from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+def kernel_source_sha() -> str:
+    src = os.path.join(ROOT, "paper_2009_12663_gb300", "csrc", "sem_step.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def traffic_record(key: str):
+    """DRAM traffic per launch of a step kernel from the committed ncu
+    summary (profiles/traffic.json), if it was taken on the current kernel
+    source; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        rec = json.load(open(path))[kernel]
+        rec = json.load(open(path))[key]
     except Exception:
         return None
-    src = os.path.join(ROOT, "paper_2009_12663_gb300", "csrc", "sem_step.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("sem_step_sha") != h:
+    if rec.get("sem_step_sha") != kernel_source_sha():
         return None
     return rec
 
@@ -339,17 +343,23 @@ def run_ours(args):
         return 0
 
     pk, pk_kind = peaks()
-    adj_bytes = ADJ_BYTES_PER_POINT * N * ph["adj_launches"]
-    achieved = adj_bytes / (ph["adj_ms"] / 1e3) / 1e9
-    fwd_achieved = FWD_BYTES_PER_POINT * N * ph["fwd_launches"] / (ph["fwd_ms"] / 1e3) / 1e9
-    tr = traffic_record("adjoint_step")
+    spl = m.schedule["shots_per_launch"]
+    tx, tz = gb.tile_shape(m.schedule["tile"])
+    adj_unit = ADJ_BYTES_PER_POINT * N * spl          # algorithmic bytes per adjoint launch
+    fwd_unit = FWD_BYTES_PER_POINT * N * spl
+    # with checkpointing the adjoint phase also replays the forward segments
+    adj_kernel_ms = ph["adj_ms"] - (ph["fwd_ms"] if args.ckpt else 0.0)
+    achieved = adj_unit * (ph["adj_launches"] // (2 if args.ckpt else 1)) / (adj_kernel_ms / 1e3) / 1e9
+    fwd_achieved = fwd_unit * ph["fwd_launches"] / (ph["fwd_ms"] / 1e3) / 1e9
+    tr = traffic_record(f"adjoint_step_{tx}x{tz}_spl{spl}")
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": (tr or {}).get("bytes_per_launch"),
-            "kernel": "sem_step_kernel<15,7,ADJ_G> (adjoint step + gradient correlation)",
-            "algorithmic_bytes_per_launch": ADJ_BYTES_PER_POINT * N,
-            "avg_launch_us": 1e3 * ph["adj_ms"] / ph["adj_launches"],
-            "peak_kind": pk_kind,
+            "kernel": f"sem_step_kernel<{tx},{tz},ADJ_G> (adjoint step + gradient correlation)",
+            "algorithmic_bytes_per_launch": adj_unit,
+            "avg_launch_us": 1e3 * adj_kernel_ms / (ph["adj_launches"] // (2 if args.ckpt else 1)),
+            "peak_kind": pk_kind, "timing": "CUDA events on the launching stream around each adjoint pass",
             "forward_kernel": {"achieved": fwd_achieved, "frac": fwd_achieved / pk["hbm_gbs"],
+                               "algorithmic_bytes_per_launch": fwd_unit,
                                "avg_launch_us": 1e3 * ph["fwd_ms"] / ph["fwd_launches"]}}
 
     cpu = None
