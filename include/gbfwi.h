@@ -137,6 +137,14 @@ int gbfwi_set_model(gbfwi_mesh *mesh, const float *rho, const float *vp, const f
  * displacements s_n = P u_n.  -> EINVAL, ENOMODEL, ECUDA, ENOMEM. */
 int gbfwi_forward(gbfwi_mesh *mesh, const int *shot_ids, int nshot, float *seis, void *stream);
 
+/* Misfit only, f = 1/2 dt sum |s - d|^2 (Eq. A1) summed over the shots: the
+ * forward simulations of gbfwi_forward and the residual reduction, without
+ * the adjoint (line searches; the forward half of an autograd wrapper).
+ * d_obs: [nshot][nrec][2][nt] in shot_ids order.  *misfit: host double.
+ * Synchronises the stream.  -> EINVAL, ENOMODEL, ENONFINITE, ECUDA, ENOMEM. */
+int gbfwi_misfit(gbfwi_mesh *mesh, const int *shot_ids, int nshot, const float *d_obs, double *misfit,
+                 void *stream);
+
 /* Misfit f = 1/2 dt sum |s - d|^2 (Eq. A1) and its exact discrete gradient
  * with respect to the nodal (rho, vp, vs) (the discrete form of Eqs.
  * A16-A18: the adjoint of the time stepping, run backwards and correlated

@@ -22,7 +22,7 @@ from ._lib import (ABI_SYMBOLS, GbfwiError, MeshDesc, Schedule, Source, check, l
                    stream_of)
 
 __all__ = [
-    "Mesh", "Bfgs", "GbfwiError", "ABI_SYMBOLS", "mesh_create", "set_model", "forward",
+    "Mesh", "Bfgs", "GbfwiError", "ABI_SYMBOLS", "mesh_create", "set_model", "forward", "misfit",
     "adjoint_gradient", "precond_diag", "bfgs_create", "bfgs_update", "bfgs_apply",
     "lowrank_invhess", "num_tiles", "tile_shape", "lib", "launch_count",
 ]
@@ -117,6 +117,13 @@ class Mesh:
               "forward")
         return seis
 
+    def misfit(self, shot_ids, d_obs) -> float:
+        ids = np.ascontiguousarray(np.asarray(shot_ids, dtype=np.int32))
+        mis = ctypes.c_double()
+        check(lib().gbfwi_misfit(self._h, ptr(ids, I32), len(ids), ptr(d_obs, F32), ctypes.byref(mis),
+                                 stream_of(d_obs)), "misfit")
+        return mis.value
+
     def adjoint_gradient(self, shot_ids, d_obs, grad, ckpt_every=-1) -> float:
         ids = np.ascontiguousarray(np.asarray(shot_ids, dtype=np.int32))
         mis = ctypes.c_double()
@@ -180,6 +187,10 @@ def set_model(mesh: Mesh, rho, vp, vs):
 
 def forward(mesh: Mesh, shot_ids, seis):
     return mesh.forward(shot_ids, seis)
+
+
+def misfit(mesh: Mesh, shot_ids, d_obs) -> float:
+    return mesh.misfit(shot_ids, d_obs)
 
 
 def adjoint_gradient(mesh: Mesh, shot_ids, d_obs, grad, ckpt_every=-1):

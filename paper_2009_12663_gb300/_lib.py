@@ -26,7 +26,7 @@ ERRORS = {
 ABI_SYMBOLS = (
     "gbfwi_mesh_create", "gbfwi_mesh_destroy", "gbfwi_mesh_dims", "gbfwi_node_coords",
     "gbfwi_num_tiles", "gbfwi_tile_shape", "gbfwi_get_schedule", "gbfwi_set_schedule",
-    "gbfwi_set_model", "gbfwi_forward", "gbfwi_adjoint_gradient", "gbfwi_precond_diag",
+    "gbfwi_set_model", "gbfwi_forward", "gbfwi_misfit", "gbfwi_adjoint_gradient", "gbfwi_precond_diag",
     "gbfwi_bfgs_create", "gbfwi_bfgs_update", "gbfwi_bfgs_count", "gbfwi_bfgs_apply",
     "gbfwi_lowrank_invhess", "gbfwi_bfgs_destroy", "gbfwi_launch_count", "gbfwi_enable_timing",
     "gbfwi_last_phase_times", "gbfwi_misfit_noalloc", "gbfwi_strerror",
@@ -80,6 +80,7 @@ def lib(path: str | None = None):
         L.gbfwi_set_schedule.argtypes = [vp, ctypes.POINTER(Schedule)]
         L.gbfwi_set_model.argtypes = [vp, vp, vp, vp, vp]
         L.gbfwi_forward.argtypes = [vp, vp, ctypes.c_int, vp, vp]
+        L.gbfwi_misfit.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double), vp]
         L.gbfwi_adjoint_gradient.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double), vp,
                                              ctypes.c_int, vp]
         L.gbfwi_precond_diag.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,

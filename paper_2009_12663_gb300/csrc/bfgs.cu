@@ -43,39 +43,66 @@ constexpr int AT = 64;          // output tile of the split-K product
 constexpr int KI = 32;          // i-chunk staged per step
 
 // part[sx][a][b] = sum_{i in split sx} A[a][i] * w[i] * Bm[b][i]
+// Tiles of 64 rows x 32 columns of A and Bm are staged through two shared
+// buffers; the global loads of the next tile are issued before the current
+// tile is consumed.
 __global__ void __launch_bounds__(256) atb_partial(const float *__restrict__ A, long long lda, int ka,
                                                    const float *__restrict__ Bm, long long ldb, int kb,
                                                    const float *__restrict__ w, long long n, long long chunk,
                                                    double *__restrict__ part)
 {
-    __shared__ float As[KI][AT + 1];
-    __shared__ float Bs[KI][AT + 1];
+    __shared__ float As[2][KI][AT + 1];
+    __shared__ float Bs[2][KI][AT + 1];
     const int sx = blockIdx.x, a0 = blockIdx.y * AT, b0 = blockIdx.z * AT;
     const long long ib = (long long)sx * chunk, ie = min(n, ib + chunk);
     const int t = threadIdx.x, ty = t / 16, tx = t % 16;
-    float acc[4][4] = {};
-    for (long long i0 = ib; i0 < ie; i0 += KI) {
-        for (int q = t; q < AT * KI; q += 256) {
+    constexpr int PER = AT * KI / 256;      // elements per thread per tile (8)
+    float ra[PER], rb[PER];
+    auto fetch = [&](long long i0) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            int q = t + u * 256;
             int r = q / KI, ii = q - r * KI;
             long long i = i0 + ii;
             bool ok = i < ie;
-            As[ii][r] = (ok && a0 + r < ka) ? A[(long long)(a0 + r) * lda + i] : 0.f;
-            float bv = (ok && b0 + r < kb) ? Bm[(long long)(b0 + r) * ldb + i] : 0.f;
-            if (w && ok) bv *= w[i];
-            Bs[ii][r] = bv;
+            ra[u] = (ok && a0 + r < ka) ? __ldg(A + (long long)(a0 + r) * lda + i) : 0.f;
+            float bv = (ok && b0 + r < kb) ? __ldg(Bm + (long long)(b0 + r) * ldb + i) : 0.f;
+            if (w && ok) bv *= __ldg(w + i);
+            rb[u] = bv;
         }
-        __syncthreads();
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            int q = t + u * 256;
+            int r = q / KI, ii = q - r * KI;
+            As[buf][ii][r] = ra[u];
+            Bs[buf][ii][r] = rb[u];
+        }
+    };
+    float acc[4][4] = {};
+    int buf = 0;
+    if (ib < ie) {
+        fetch(ib);
+        stash(0);
+    }
+    __syncthreads();
+    for (long long i0 = ib; i0 < ie; i0 += KI) {
+        const bool more = i0 + KI < ie;
+        if (more) fetch(i0 + KI);
 #pragma unroll 8
         for (int ii = 0; ii < KI; ++ii) {
             float av[4], bv[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) { av[u] = As[ii][ty * 4 + u]; bv[u] = Bs[ii][tx * 4 + u]; }
+            for (int u = 0; u < 4; ++u) { av[u] = As[buf][ii][ty * 4 + u]; bv[u] = Bs[buf][ii][tx * 4 + u]; }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
         }
+        if (more) stash(buf ^ 1);
         __syncthreads();
+        buf ^= 1;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -119,7 +146,28 @@ __global__ void __launch_bounds__(128) combine_kernel(const float *__restrict__ 
         float acc[CB];
 #pragma unroll
         for (int cc = 0; cc < CB; ++cc) acc[cc] = 0.f;
-        for (int a = 0; a < ktot; ++a) {
+        int a = 0;
+        for (; a + 4 <= ktot; a += 4) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float *row = (a + u) < k1 ? A1 + (long long)(a + u) * lda : A2 + (long long)(a + u - k1) * lda;
+                v[u] = __ldg(row + i);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 *c4 = cs4 + (a + u) * (CB / 4);
+#pragma unroll
+                for (int q = 0; q < CB / 4; ++q) {
+                    float4 c = c4[q];
+                    acc[4 * q + 0] = fmaf(c.x, v[u], acc[4 * q + 0]);
+                    acc[4 * q + 1] = fmaf(c.y, v[u], acc[4 * q + 1]);
+                    acc[4 * q + 2] = fmaf(c.z, v[u], acc[4 * q + 2]);
+                    acc[4 * q + 3] = fmaf(c.w, v[u], acc[4 * q + 3]);
+                }
+            }
+        }
+        for (; a < ktot; ++a) {
             const float *row = a < k1 ? A1 + (long long)a * lda : A2 + (long long)(a - k1) * lda;
             float v = __ldg(row + i);
             const float4 *c4 = cs4 + a * (CB / 4);
@@ -232,11 +280,13 @@ __global__ void chol_kernel(const double *__restrict__ G, int p, double *__restr
 // (round-robin pairs), eigenpairs ordered by |lambda| descending.
 // work: >= 4 p^2 + 4 p doubles; outputs lam[rank] FP64 and coef[rank][p] = U^T.
 __global__ void omega_eig_kernel(const double *__restrict__ R1, const double *__restrict__ R2,
-                                 const double *__restrict__ M1, int p, int rank, double *__restrict__ work,
+                                 const double *__restrict__ M1, int p, int rank, double *work,
                                  double *__restrict__ lam, float *__restrict__ coef, int *__restrict__ flag,
-                                 int max_sweeps)
+                                 int max_sweeps, int use_smem)
 {
     const int t = threadIdx.x, nt = blockDim.x;
+    extern __shared__ double smem_work[];
+    if (use_smem) work = smem_work;         // small p: the whole workspace in shared memory
     double *Aug = work;                     // [p][2p]: [M1^T | Rt^T]
     double *A = Aug + 2LL * p * p;          // [p][p] symmetric matrix
     double *U = A + (long long)p * p;       // [p][p]
@@ -696,8 +746,15 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
     float *Qf = E;
     // 3. M1 = Q^T X ; Omega (Q^T X) = R2 R1 ; eigenpairs
     GB_TRY(atb(h, Qf, n, p, Xd, n, p, nullptr, M1, p, s));
-    omega_eig_kernel<<<1, 256, 0, s>>>(R1, R2, M1, p, rank, work, lam, coef, flag, 60);
-    GB_LAUNCHED();
+    {
+        const size_t ws = (4 * pp + 4 * (size_t)p) * sizeof(double);
+        const int use_smem = ws <= 200 * 1024;
+        if (use_smem)
+            GB_CUDA(cudaFuncSetAttribute(omega_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
+        omega_eig_kernel<<<1, 512, use_smem ? ws : 0, s>>>(R1, R2, M1, p, rank, work, lam, coef, flag, 60,
+                                                          use_smem);
+        GB_LAUNCHED();
+    }
     // 4. V = Q U (first `rank` columns)
     const bool devV = V && gb_is_device_ptr(V);
     float *Vd = devV ? V : Q;     // Q buffer is free now

@@ -125,6 +125,12 @@ struct gbfwi_mesh {
         w_red, w_flag, w_shots, w_tmp, w_stage;
     DevBuf w_pc;        // preconditioner accumulators
 
+    DevBuf w_batch;     // shot ids of the batch being replayed (fixed address for graphs)
+    // CUDA graphs of whole forward / adjoint passes, keyed by schedule,
+    // batch size and work-buffer addresses
+    std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;
+    cudaStream_t cap_stream = nullptr;
+
     // optional per-phase timing of adjoint_gradient
     bool timing = false;
     std::vector<cudaEvent_t> ev;        // 4 per shot batch
@@ -174,6 +180,7 @@ struct StepArgs {
 };
 
 int gb_launch_step(int mode, int tile, const StepArgs &a, int nbatch, cudaStream_t s);
+int gb_prepare_step(int mode, int tile);   // set kernel attributes outside any stream capture
 
 // small kernels of the SEM driver
 int gb_material(gbfwi_mesh *m, cudaStream_t s);

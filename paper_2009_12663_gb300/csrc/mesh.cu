@@ -30,6 +30,8 @@ extern "C" long long gbfwi_launch_count(void) { return g_launches.load(std::memo
 gbfwi_mesh::~gbfwi_mesh()
 {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
 }
 
 extern "C" int gbfwi_enable_timing(gbfwi_mesh *m, int on)

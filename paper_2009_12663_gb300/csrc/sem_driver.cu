@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <string>
 #include <vector>
 
 #include "gbfwi_internal.h"
@@ -400,6 +401,64 @@ extern "C" int gbfwi_forward(gbfwi_mesh *m, const int *shot_ids, int nshot, floa
 }
 
 // ---------------------------------------------------------------------------
+// misfit only
+// ---------------------------------------------------------------------------
+
+extern "C" int gbfwi_misfit(gbfwi_mesh *m, const int *shot_ids, int nshot, const float *d_obs, double *misfit,
+                            void *stream)
+{
+    if (!m || !d_obs || !misfit) return GBFWI_EINVAL;
+    GB_TRY(check_shots(m, shot_ids, nshot));
+    if (!m->have_model) return GBFWI_ENOMODEL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int tile = m->sch.tile;
+    GB_TRY(gb_build_tile_lists(m, tile));
+    const int nt = m->d.nt;
+    const long long NP = (long long)m->nz * m->pitch;
+    const int Bmax = std::min(m->sch.shots_per_launch, nshot);
+    const size_t seis_shot = (size_t)m->nrec * 2 * nt;
+    GB_TRY(m->w_hist.ensure((size_t)3 * Bmax * NP * sizeof(float2)));
+    GB_TRY(m->w_vh.ensure((size_t)Bmax * NP * sizeof(float2)));
+    GB_TRY(m->w_shots.ensure((size_t)nshot * sizeof(int)));
+    GB_TRY(m->w_seis.ensure(seis_shot * Bmax * sizeof(float)));
+    GB_TRY(m->w_red.ensure((1024 + 8) * sizeof(double) + 4096));
+    GB_TRY(m->w_flag.ensure(16));
+    const void *obs_d = nullptr;
+    GB_TRY(stage_in(m->w_obs, d_obs, seis_shot * nshot * sizeof(float), s, &obs_d));
+    double *partial = m->w_red.as<double>();
+    double *mis_d = partial + 1024;
+    int *flag = m->w_flag.as<int>();
+    GB_CUDA(cudaMemcpyAsync(m->w_shots.p, shot_ids, nshot * sizeof(int), cudaMemcpyHostToDevice, s));
+    GB_CUDA(cudaMemsetAsync(mis_d, 0, sizeof(double), s));
+    GB_CUDA(cudaMemsetAsync(flag, 0, 16, s));
+    for (int i0 = 0; i0 < nshot; i0 += Bmax) {
+        int B = std::min(Bmax, nshot - i0);
+        Ctx c{m, &m->lists[tile], tile, B, s, m->w_shots.as<int>() + i0, NP};
+        float2 *ring = m->w_hist.as<float2>();
+        long long lev = (long long)B * NP;
+        GB_CUDA(cudaMemsetAsync(ring, 0, 3 * lev * sizeof(float2), s));
+        GB_CUDA(cudaMemsetAsync(m->w_vh.p, 0, lev * sizeof(float2), s));
+        SlotFn slot = [&](int k) { return ring + (long long)(k % 3) * lev; };
+        float *seis_d = m->w_seis.as<float>();
+        GB_TRY(fwd_range(c, MODE_FWD, 0, nt, slot, m->w_vh.as<float2>(), seis_d, nullptr, 0, 0));
+        const int nblk = 1024;
+        residual_kernel<<<nblk, 256, 0, s>>>(seis_d, (const float *)obs_d + seis_shot * i0,
+                                              (long long)seis_shot * B, partial, flag);
+        GB_LAUNCHED();
+        misfit_finish<<<1, 32, 0, s>>>(partial, nblk, 0.5 * m->d.dt, mis_d);
+        GB_LAUNCHED();
+    }
+    double mis_h = 0;
+    int flag_h = 0;
+    GB_CUDA(cudaMemcpyAsync(&mis_h, mis_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(&flag_h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (flag_h || !std::isfinite(mis_h)) return GBFWI_ENONFINITE;
+    *misfit = mis_h;
+    return GBFWI_OK;
+}
+
+// ---------------------------------------------------------------------------
 // forward pass with history (full) or snapshots (checkpointed) for one batch
 // ---------------------------------------------------------------------------
 
@@ -496,6 +555,61 @@ int adjoint_pass(const Ctx &c, BatchHist &h, int mode, const float *sig, float *
     return GBFWI_OK;
 }
 
+// Run body() on the caller's stream s, or, with graphs enabled, replay a CUDA
+// graph of it captured once on a private stream (the caller's stream may be
+// the legacy default stream, which cannot be captured).
+int run_pass(gbfwi_mesh *m, const std::string &key, cudaStream_t s, const std::function<int(cudaStream_t)> &body)
+{
+    if (!m->sch.use_graph) return body(s);
+    for (auto &g : m->graphs)
+        if (g.first == key) {
+            GB_CUDA(cudaGraphLaunch(g.second, s));
+            return GBFWI_OK;
+        }
+    if (!m->cap_stream) GB_CUDA(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
+    // the capture stream must not run ahead of work already queued on s
+    cudaEvent_t ready;
+    GB_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    GB_CUDA(cudaEventRecord(ready, s));
+    GB_CUDA(cudaStreamWaitEvent(m->cap_stream, ready, 0));
+    GB_CUDA(cudaEventDestroy(ready));
+    GB_CUDA(cudaStreamSynchronize(m->cap_stream));
+    GB_CUDA(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = body(m->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(m->cap_stream, &graph);
+    if (rc != GBFWI_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (rc == GBFWI_OK) {
+            gb_set_last_cuda_error(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
+            rc = GBFWI_ECUDA;
+        }
+        return rc;
+    }
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+        gb_set_last_cuda_error(ce, "cudaGraphInstantiate", __FILE__, __LINE__);
+        return GBFWI_ECUDA;
+    }
+    if (m->graphs.size() >= 16) {          // bounded cache
+        cudaGraphExecDestroy(m->graphs.front().second);
+        m->graphs.erase(m->graphs.begin());
+    }
+    m->graphs.emplace_back(key, exec);
+    GB_CUDA(cudaGraphLaunch(exec, s));
+    return GBFWI_OK;
+}
+
+std::string pass_key(const char *what, const gbfwi_mesh *m, int B, int ckpt, std::initializer_list<const void *> ptrs)
+{
+    std::string k = what;
+    k += "|" + std::to_string(m->sch.tile) + "|" + std::to_string(B) + "|" + std::to_string(ckpt);
+    for (const void *p : ptrs) k += "|" + std::to_string((uintptr_t)p);
+    return k;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -561,12 +675,26 @@ extern "C" int gbfwi_adjoint_gradient(gbfwi_mesh *m, const int *shot_ids, int ns
         return GBFWI_OK;
     };
 
+    GB_TRY(m->w_batch.ensure((size_t)Bmax * sizeof(int)));
+    GB_TRY(gb_prepare_step(MODE_FWD, tile));
+    GB_TRY(gb_prepare_step(MODE_ADJ_G, tile));
     for (int i0 = 0, bi = 0; i0 < nshot; i0 += Bmax, ++bi) {
         int B = std::min(Bmax, nshot - i0);
-        Ctx c{m, &m->lists[tile], tile, B, s, m->w_shots.as<int>() + i0, NP};
+        // this batch's source ids at a fixed address, so that captured passes replay for every batch
+        GB_CUDA(cudaMemcpyAsync(m->w_batch.p, m->w_shots.as<int>() + i0, B * sizeof(int),
+                                cudaMemcpyDeviceToDevice, s));
+        Ctx c{m, &m->lists[tile], tile, B, s, m->w_batch.as<int>(), NP};
         float *seis_d = m->w_seis.as<float>();
+        const std::string kf = pass_key("fwd", m, B, h.C,
+                                        {m->w_hist.p, m->w_vh.p, m->w_seis.p, m->w_snap.p, m->w_batch.p});
+        const std::string ka = pass_key("adj", m, B, h.C,
+                                        {m->w_hist.p, m->w_seis.p, m->w_snap.p, m->w_adj.p, m->w_wh.p, m->w_acc.p});
         GB_TRY(mark(4 * bi));
-        GB_TRY(forward_pass(c, h, seis_d));
+        GB_TRY(run_pass(m, kf, s, [&](cudaStream_t cs) {
+            Ctx cc = c;
+            cc.s = cs;
+            return forward_pass(cc, h, seis_d);
+        }));
         GB_TRY(mark(4 * bi + 1));
         m->fwd_launches += nt;
         // residual r = s - d (in place) and misfit 1/2 dt sum r^2
@@ -579,7 +707,11 @@ extern "C" int gbfwi_adjoint_gradient(gbfwi_mesh *m, const int *shot_ids, int ns
         float *acc = m->w_acc.as<float>();
         GB_CUDA(cudaMemsetAsync(acc, 0, (size_t)B * 5 * NP * sizeof(float), s));
         GB_TRY(mark(4 * bi + 2));
-        GB_TRY(adjoint_pass(c, h, MODE_ADJ_G, seis_d, acc, 5 * NP, NP));
+        GB_TRY(run_pass(m, ka, s, [&](cudaStream_t cs) {
+            Ctx cc = c;
+            cc.s = cs;
+            return adjoint_pass(cc, h, MODE_ADJ_G, seis_d, acc, 5 * NP, NP);
+        }));
         GB_TRY(mark(4 * bi + 3));
         m->adj_launches += (h.C == 0) ? nt : 2LL * nt;
         acc_reduce<<<grid_for(5 * NP), 256, 0, s>>>(acc, B, 5, NP, tot);

@@ -511,18 +511,25 @@ static size_t step_smem()
 }
 
 template <int TX, int TZ, int MODE>
+static int prepare_one()
+{
+    static bool attr_done[64] = {};          // per device ordinal
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+        GB_CUDA(cudaFuncSetAttribute(sem_step_kernel<TX, TZ, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)step_smem<TX, TZ, MODE>()));
+        attr_done[dev] = true;
+    }
+    return GBFWI_OK;
+}
+
+template <int TX, int TZ, int MODE>
 static int launch_one(const StepArgs &a, int nbatch, cudaStream_t s)
 {
     constexpr int NE = (TX + 1) * (TZ + 1);
     size_t smem = step_smem<TX, TZ, MODE>();
-    static bool attr_done[64] = {};          // per device ordinal
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 64 && !attr_done[dev]) {
-        GB_CUDA(cudaFuncSetAttribute(sem_step_kernel<TX, TZ, MODE>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_done[dev] = true;
-    }
+    GB_TRY((prepare_one<TX, TZ, MODE>()));
     dim3 grid((a.nex + TX - 1) / TX, (a.nez + TZ - 1) / TZ, nbatch);
     sem_step_kernel<TX, TZ, MODE><<<grid, NE, smem, s>>>(a);
     GB_LAUNCHED();
@@ -537,6 +544,30 @@ static int launch_mode(int mode, const StepArgs &a, int nbatch, cudaStream_t s)
     case MODE_FWD_PC: return launch_one<TX, TZ, MODE_FWD_PC>(a, nbatch, s);
     case MODE_ADJ_G: return launch_one<TX, TZ, MODE_ADJ_G>(a, nbatch, s);
     case MODE_ADJ_PC: return launch_one<TX, TZ, MODE_ADJ_PC>(a, nbatch, s);
+    }
+    return GBFWI_EINVAL;
+}
+
+template <int TX, int TZ>
+static int prepare_mode(int mode)
+{
+    switch (mode) {
+    case MODE_FWD: return prepare_one<TX, TZ, MODE_FWD>();
+    case MODE_FWD_PC: return prepare_one<TX, TZ, MODE_FWD_PC>();
+    case MODE_ADJ_G: return prepare_one<TX, TZ, MODE_ADJ_G>();
+    case MODE_ADJ_PC: return prepare_one<TX, TZ, MODE_ADJ_PC>();
+    }
+    return GBFWI_EINVAL;
+}
+
+int gb_prepare_step(int mode, int tile)
+{
+    switch (tile) {
+    case 0: return prepare_mode<15, 7>(mode);
+    case 1: return prepare_mode<7, 15>(mode);
+    case 2: return prepare_mode<7, 7>(mode);
+    case 3: return prepare_mode<15, 15>(mode);
+    case 4: return prepare_mode<31, 3>(mode);
     }
     return GBFWI_EINVAL;
 }

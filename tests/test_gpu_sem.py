@@ -165,6 +165,29 @@ def test_batched_shots_equal_single_shot_launches(c2):
     assert np.array_equal(g1, g2)
 
 
+def test_graph_replay_equals_eager_launches(c2):
+    ref = c2.gpu_gradient(c2.mesh(shots_per_launch=1), [0, 1], obs=c2.obs_gpu)
+    for sched in (dict(shots_per_launch=1, use_graph=1), dict(shots_per_launch=2, use_graph=1, ckpt_every=77),
+                  dict(shots_per_launch=1, use_graph=1, tile=3)):
+        m = c2.mesh(**sched)
+        for _ in range(2):                                  # capture, then replay
+            f, g = c2.gpu_gradient(m, [0, 1], obs=c2.obs_gpu)
+            assert f == ref[0] and np.array_equal(g, ref[1]), sched
+
+
+def test_autotuner_returns_a_valid_schedule(c2):
+    from paper_2009_12663_gb300 import autotune
+    wl = c2.wl
+    model = [t32(a) for a in c2.start]
+    best, timings = autotune.tune(wl.nex, wl.nez, wl.h, wl.dt, wl.nt, c2.srcs, wl.rec_xz, model,
+                                  spl_options=(1, 2), tiles=(0, 2), probe_nt=40, use_cache=False)
+    assert len(timings) == 8
+    m = c2.mesh(**best)
+    f, g = c2.gpu_gradient(m, [0, 1], obs=c2.obs_gpu)
+    ref = c2.gpu_gradient(c2.mesh(), [0, 1], obs=c2.obs_gpu)
+    assert f == ref[0] and np.array_equal(g, ref[1])
+
+
 def test_checkpointed_gradient_equals_full_history(c1):
     f0, g0 = c1.gpu_gradient(c1.mesh(), [0], ckpt=0)
     for C in (97, 400):
