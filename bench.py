@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--shots-per-launch", type=int, default=1)
     ap.add_argument("--ckpt", type=int, default=0)
     ap.add_argument("--graph", type=int, default=0, help="1: replay the time loops as CUDA graphs")
+    ap.add_argument("--streams", type=int, default=1, help="shot batches simulated concurrently")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -231,7 +232,8 @@ def run_ours(args):
     srcs = wl.sources(amp=1e12)
     m = gb.Mesh(wl.nex, wl.nez, wl.h, wl.dt, wl.nt, srcs, wl.rec_xz, free_surface_top=1)
     tile = args.tile if args.tile is not None else 0
-    m.set_schedule(shots_per_launch=args.shots_per_launch, tile=tile, use_graph=args.graph, ckpt_every=args.ckpt)
+    m.set_schedule(shots_per_launch=args.shots_per_launch, tile=tile, use_graph=args.graph, ckpt_every=args.ckpt,
+                   streams=args.streams)
     x, z = m.node_coords()
     W, H = wl.nex * wl.h, wl.nez * wl.h
     seed = 2024 + rank

@@ -93,6 +93,9 @@ typedef struct {
     int ckpt_every;         /* 0: keep the whole forward history on the device;
                                k > 0: keep a snapshot every k steps and
                                recompute each segment during the adjoint */
+    int streams;            /* shot batches simulated concurrently on separate
+                               library streams by gbfwi_adjoint_gradient (1..8);
+                               each keeps its own history */
 } gbfwi_schedule;
 
 /* ---------------------------------------------------------------- mesh -- */

@@ -91,10 +91,10 @@ class Mesh:
         s = Schedule()
         check(lib().gbfwi_get_schedule(self._h, ctypes.byref(s)), "get_schedule")
         return dict(shots_per_launch=s.shots_per_launch, tile=s.tile, use_graph=s.use_graph,
-                    ckpt_every=s.ckpt_every)
+                    ckpt_every=s.ckpt_every, streams=s.streams)
 
-    def set_schedule(self, shots_per_launch=1, tile=0, use_graph=0, ckpt_every=0):
-        s = Schedule(int(shots_per_launch), int(tile), int(use_graph), int(ckpt_every))
+    def set_schedule(self, shots_per_launch=1, tile=0, use_graph=0, ckpt_every=0, streams=1):
+        s = Schedule(int(shots_per_launch), int(tile), int(use_graph), int(ckpt_every), int(streams))
         check(lib().gbfwi_set_schedule(self._h, ctypes.byref(s)), "set_schedule")
 
     def enable_timing(self, on=True):

@@ -53,7 +53,7 @@ class Source(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("shots_per_launch", ctypes.c_int), ("tile", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("ckpt_every", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("ckpt_every", ctypes.c_int), ("streams", ctypes.c_int)]
 
 
 _LIB = None

@@ -104,7 +104,7 @@ struct gbfwi_mesh {
     std::vector<std::vector<SrcNode>> src_nodes;
     // assembled 1-D quadrature weights (metres): W_g = wx[ix] * wz[iz]
     std::vector<double> wx1, wz1;
-    gbfwi_schedule sch{1, 0, 0, 0};
+    gbfwi_schedule sch{1, 0, 0, 0, 1};
     bool have_model = false;
     double dx_min = 0;                   // smallest GLL node spacing
 
@@ -126,6 +126,14 @@ struct gbfwi_mesh {
     DevBuf w_pc;        // preconditioner accumulators
 
     DevBuf w_batch;     // shot ids of the batch being replayed (fixed address for graphs)
+    DevBuf w_lacc;      // gradient accumulators of the batch in flight (fixed address for graphs)
+    // extra concurrent lanes of adjoint_gradient (lane 0 uses the buffers above)
+    struct Lane {
+        DevBuf hist, snap, vh, adj, wh, seis, batch, acc;
+        cudaStream_t st = nullptr;
+        ~Lane() { if (st) cudaStreamDestroy(st); }
+    };
+    std::vector<Lane *> lanes;
     // CUDA graphs of whole forward / adjoint passes, keyed by schedule,
     // batch size and work-buffer addresses
     std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;

@@ -32,6 +32,7 @@ gbfwi_mesh::~gbfwi_mesh()
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     for (auto &g : graphs) cudaGraphExecDestroy(g.second);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (Lane *l : lanes) delete l;
 }
 
 extern "C" int gbfwi_enable_timing(gbfwi_mesh *m, int on)
@@ -373,7 +374,7 @@ extern "C" int gbfwi_set_schedule(gbfwi_mesh *m, const gbfwi_schedule *s)
 {
     if (!m || !s) return GBFWI_EINVAL;
     if (s->shots_per_launch < 1 || s->tile < 0 || s->tile >= kNumTiles || s->ckpt_every < 0 ||
-        (s->use_graph != 0 && s->use_graph != 1))
+        (s->use_graph != 0 && s->use_graph != 1) || s->streams < 1 || s->streams > 8)
         return GBFWI_EINVAL;
     m->sch = *s;
     return GBFWI_OK;

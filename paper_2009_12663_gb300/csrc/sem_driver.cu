@@ -133,16 +133,22 @@ int adj_range(const Ctx &c, int mode, int j0, int j1, float2 *wring, float2 *wh,
 
 // ------------------------------------------------------------------ kernels
 
-__global__ void residual_kernel(float *__restrict__ syn, const float *__restrict__ obs, long long n,
+// r = s - d in place, per-shot partial sums of r^2: grid (kMisfitBlocks, B)
+constexpr int kMisfitBlocks = 64;
+
+__global__ void residual_kernel(float *__restrict__ syn, const float *__restrict__ obs, long long per_shot,
                                 double *__restrict__ partial, int *__restrict__ flag)
 {
+    const int shot = blockIdx.y;
+    float *s = syn + (long long)shot * per_shot;
+    const float *d = obs + (long long)shot * per_shot;
     double acc = 0.0;
     int bad = 0;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < per_shot;
          q += (long long)gridDim.x * blockDim.x) {
-        float r = syn[q] - obs[q];
+        float r = s[q] - d[q];
         if (!isfinite(r)) bad = 1;
-        syn[q] = r;
+        s[q] = r;
         acc += (double)r * (double)r;
     }
     __shared__ double red[256];
@@ -152,17 +158,23 @@ __global__ void residual_kernel(float *__restrict__ syn, const float *__restrict
         if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+    if (threadIdx.x == 0) partial[shot * kMisfitBlocks + blockIdx.x] = red[0];
     if (bad) atomicOr(flag, 1);
 }
 
-__global__ void misfit_finish(const double *__restrict__ partial, int nblk, double half_dt,
+// total += 1/2 dt sum_b partial[s][b], shot by shot in order, so the result
+// does not depend on how the shots were batched
+__global__ void misfit_finish(const double *__restrict__ partial, int nshot, double half_dt,
                               double *__restrict__ total)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += partial[b];
-        *total += half_dt * s;
+        double t = *total;
+        for (int sh = 0; sh < nshot; ++sh) {
+            double s = 0.0;
+            for (int b = 0; b < kMisfitBlocks; ++b) s += partial[sh * kMisfitBlocks + b];
+            t += half_dt * s;
+        }
+        *total = t;
     }
 }
 
@@ -188,16 +200,19 @@ __global__ void acc_reduce(const float *__restrict__ acc, int B, int ncomp, long
     }
 }
 
-// gradient chain rule: (g_lambda, g_mu, g_M, g_Zp, g_Zs) -> (rho, vp, vs), times -dt^2
-__global__ void chain_kernel(const float *__restrict__ tot, const float *__restrict__ model, int nx,
-                             int nz, int pitch, float mdt2, float *__restrict__ grad)
+// gradient chain rule: (g_lambda, g_mu, sum u.a^w, g_Zp, g_Zs) -> (rho, vp, vs), times -dt^2;
+// dM_g/drho_g = W_g = wx[ix] wz[iz]
+__global__ void chain_kernel(const float *__restrict__ tot, const float *__restrict__ model,
+                             const float *__restrict__ wx, const float *__restrict__ wz, int nx, int nz,
+                             int pitch, float mdt2, float *__restrict__ grad)
 {
     long long NP = (long long)nz * pitch, N = (long long)nz * nx;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
          q += (long long)gridDim.x * blockDim.x) {
         int iz = (int)(q / nx), ix = (int)(q - (long long)iz * nx);
         long long g = (long long)iz * pitch + ix;
-        float gl = tot[g], gm = tot[NP + g], gM = tot[2 * NP + g], gp = tot[3 * NP + g], gs = tot[4 * NP + g];
+        float gl = tot[g], gm = tot[NP + g], gp = tot[3 * NP + g], gs = tot[4 * NP + g];
+        float gM = wx[ix] * wz[iz] * tot[2 * NP + g];
         float r = model[g], p = model[NP + g], s = model[2 * NP + g];
         float grho = gl * (p * p - 2.f * s * s) + gm * s * s + gM + gp * p + gs * s;
         float gvp = gl * (2.f * r * p) + gp * r;
@@ -421,12 +436,13 @@ extern "C" int gbfwi_misfit(gbfwi_mesh *m, const int *shot_ids, int nshot, const
     GB_TRY(m->w_vh.ensure((size_t)Bmax * NP * sizeof(float2)));
     GB_TRY(m->w_shots.ensure((size_t)nshot * sizeof(int)));
     GB_TRY(m->w_seis.ensure(seis_shot * Bmax * sizeof(float)));
-    GB_TRY(m->w_red.ensure((1024 + 8) * sizeof(double) + 4096));
+    const int npart = kMisfitBlocks * Bmax;
+    GB_TRY(m->w_red.ensure((size_t)(npart + 8) * sizeof(double) + 4096));
     GB_TRY(m->w_flag.ensure(16));
     const void *obs_d = nullptr;
     GB_TRY(stage_in(m->w_obs, d_obs, seis_shot * nshot * sizeof(float), s, &obs_d));
     double *partial = m->w_red.as<double>();
-    double *mis_d = partial + 1024;
+    double *mis_d = partial + npart;
     int *flag = m->w_flag.as<int>();
     GB_CUDA(cudaMemcpyAsync(m->w_shots.p, shot_ids, nshot * sizeof(int), cudaMemcpyHostToDevice, s));
     GB_CUDA(cudaMemsetAsync(mis_d, 0, sizeof(double), s));
@@ -441,11 +457,10 @@ extern "C" int gbfwi_misfit(gbfwi_mesh *m, const int *shot_ids, int nshot, const
         SlotFn slot = [&](int k) { return ring + (long long)(k % 3) * lev; };
         float *seis_d = m->w_seis.as<float>();
         GB_TRY(fwd_range(c, MODE_FWD, 0, nt, slot, m->w_vh.as<float2>(), seis_d, nullptr, 0, 0));
-        const int nblk = 1024;
-        residual_kernel<<<nblk, 256, 0, s>>>(seis_d, (const float *)obs_d + seis_shot * i0,
-                                              (long long)seis_shot * B, partial, flag);
+        residual_kernel<<<dim3(kMisfitBlocks, B), 256, 0, s>>>(seis_d, (const float *)obs_d + seis_shot * i0,
+                                                              (long long)seis_shot, partial, flag);
         GB_LAUNCHED();
-        misfit_finish<<<1, 32, 0, s>>>(partial, nblk, 0.5 * m->d.dt, mis_d);
+        misfit_finish<<<1, 32, 0, s>>>(partial, B, 0.5 * m->d.dt, mis_d);
         GB_LAUNCHED();
     }
     double mis_h = 0;
@@ -470,16 +485,30 @@ struct BatchHist {
     float2 *seg = nullptr;     // ckpt > 0: C + 2 slots
     float2 *snap = nullptr;    // ckpt > 0: [nseg][3][B][NP]: u_{sC}, u_{sC+1}, vh_{sC}
     float2 *vh_rec = nullptr;  // recompute velocity
+    float2 *vh = nullptr;      // forward half-step velocity
+    float2 *wring = nullptr;   // adjoint field, 3 levels
+    float2 *wh = nullptr;      // adjoint half-step velocity
     int C = 0, nseg = 0;
 };
 
-int alloc_hist(gbfwi_mesh *m, int B, int ckpt, long long NP, BatchHist &h)
+// the work buffers of one concurrent lane
+struct LaneRef {
+    DevBuf *hist, *snap, *vh, *adj, *wh, *seis, *batch, *acc;
+    cudaStream_t st;
+};
+
+LaneRef lane0(gbfwi_mesh *m, cudaStream_t s)
+{
+    return LaneRef{&m->w_hist, &m->w_snap, &m->w_vh, &m->w_adj, &m->w_wh, &m->w_seis, &m->w_batch, &m->w_lacc, s};
+}
+
+int alloc_hist(gbfwi_mesh *m, const LaneRef &L, int B, int ckpt, long long NP, BatchHist &h, bool adjoint)
 {
     const int nt = m->d.nt;
     long long lev = (long long)B * NP;
     if (ckpt <= 0 || ckpt >= nt) {
-        GB_TRY(m->w_hist.ensure((size_t)(nt + 2) * lev * sizeof(float2)));
-        h.full.base = m->w_hist.as<float2>();
+        GB_TRY(L.hist->ensure((size_t)(nt + 2) * lev * sizeof(float2)));
+        h.full.base = L.hist->as<float2>();
         h.full.slots = nt + 2;
         h.full.kbase = 0;
         h.full.lev = lev;
@@ -488,12 +517,20 @@ int alloc_hist(gbfwi_mesh *m, int B, int ckpt, long long NP, BatchHist &h)
         h.C = ckpt;
         h.nseg = (nt + ckpt - 1) / ckpt;
         size_t ring = 3, seg = (size_t)ckpt + 2, snap = (size_t)h.nseg * 3, vrec = 1;
-        GB_TRY(m->w_hist.ensure((ring + seg + vrec) * lev * sizeof(float2)));
-        GB_TRY(m->w_snap.ensure(snap * lev * sizeof(float2)));
-        h.ring = m->w_hist.as<float2>();
+        GB_TRY(L.hist->ensure((ring + seg + vrec) * lev * sizeof(float2)));
+        GB_TRY(L.snap->ensure(snap * lev * sizeof(float2)));
+        h.ring = L.hist->as<float2>();
         h.seg = h.ring + ring * lev;
         h.vh_rec = h.seg + seg * lev;
-        h.snap = m->w_snap.as<float2>();
+        h.snap = L.snap->as<float2>();
+    }
+    GB_TRY(L.vh->ensure(lev * sizeof(float2)));
+    h.vh = L.vh->as<float2>();
+    if (adjoint) {
+        GB_TRY(L.adj->ensure(3 * lev * sizeof(float2)));
+        GB_TRY(L.wh->ensure(lev * sizeof(float2)));
+        h.wring = L.adj->as<float2>();
+        h.wh = L.wh->as<float2>();
     }
     return GBFWI_OK;
 }
@@ -504,7 +541,7 @@ int forward_pass(const Ctx &c, BatchHist &h, float *seis)
     gbfwi_mesh *m = c.m;
     const int nt = m->d.nt;
     const long long lev = (long long)c.B * c.NP;
-    float2 *vh = m->w_vh.as<float2>();
+    float2 *vh = h.vh;
     GB_CUDA(cudaMemsetAsync(vh, 0, lev * sizeof(float2), c.s));
     if (h.C == 0) {
         GB_CUDA(cudaMemsetAsync(h.full.base, 0, 2 * lev * sizeof(float2), c.s));
@@ -531,8 +568,8 @@ int adjoint_pass(const Ctx &c, BatchHist &h, int mode, const float *sig, float *
     gbfwi_mesh *m = c.m;
     const int nt = m->d.nt;
     const long long lev = (long long)c.B * c.NP;
-    float2 *wring = m->w_adj.as<float2>();
-    float2 *wh = m->w_wh.as<float2>();
+    float2 *wring = h.wring;
+    float2 *wh = h.wh;
     GB_CUDA(cudaMemsetAsync(wring, 0, 3 * lev * sizeof(float2), c.s));
     GB_CUDA(cudaMemsetAsync(wh, 0, lev * sizeof(float2), c.s));
     if (h.C == 0) {
@@ -631,18 +668,32 @@ extern "C" int gbfwi_adjoint_gradient(gbfwi_mesh *m, const int *shot_ids, int ns
     const long long N = (long long)m->nz * m->nx;
     const int Bmax = std::min(m->sch.shots_per_launch, nshot);
     const size_t seis_shot = (size_t)m->nrec * 2 * nt;
-    const long long lev = (long long)Bmax * NP;
+    const int nbatch = (nshot + Bmax - 1) / Bmax;
+    const int L = std::max(1, std::min(m->sch.streams, nbatch));
 
-    BatchHist h;
-    GB_TRY(alloc_hist(m, Bmax, ckpt, NP, h));
-    GB_TRY(m->w_vh.ensure(lev * sizeof(float2)));
-    GB_TRY(m->w_adj.ensure(3 * lev * sizeof(float2)));
-    GB_TRY(m->w_wh.ensure(lev * sizeof(float2)));
-    GB_TRY(m->w_acc.ensure((size_t)Bmax * 5 * NP * sizeof(float)));
+    // lanes: 0 = the mesh's own buffers on the caller's stream, 1.. = extra streams
+    while ((int)m->lanes.size() < L - 1) m->lanes.push_back(new gbfwi_mesh::Lane());
+    std::vector<LaneRef> lanes{lane0(m, s)};
+    for (int l = 1; l < L; ++l) {
+        gbfwi_mesh::Lane *ln = m->lanes[l - 1];
+        if (!ln->st) GB_CUDA(cudaStreamCreateWithFlags(&ln->st, cudaStreamNonBlocking));
+        lanes.push_back(
+            LaneRef{&ln->hist, &ln->snap, &ln->vh, &ln->adj, &ln->wh, &ln->seis, &ln->batch, &ln->acc, ln->st});
+    }
+    std::vector<BatchHist> hs(L);
+    for (int l = 0; l < L; ++l) {
+        GB_TRY(alloc_hist(m, lanes[l], Bmax, ckpt, NP, hs[l], true));
+        GB_TRY(lanes[l].seis->ensure(seis_shot * Bmax * sizeof(float)));
+        GB_TRY(lanes[l].batch->ensure((size_t)Bmax * sizeof(int)));
+        GB_TRY(lanes[l].acc->ensure((size_t)Bmax * 5 * NP * sizeof(float)));
+    }
+    // per-shot accumulators and misfit partials, reduced once in shot order at
+    // the end: the result does not depend on batching or lanes
+    GB_TRY(m->w_acc.ensure((size_t)nshot * 5 * NP * sizeof(float)));
     GB_TRY(m->w_grad.ensure((size_t)5 * NP * sizeof(float)));
-    GB_TRY(m->w_seis.ensure(seis_shot * Bmax * sizeof(float)));
     GB_TRY(m->w_shots.ensure((size_t)nshot * sizeof(int)));
-    GB_TRY(m->w_red.ensure((1024 + 8) * sizeof(double)));
+    const int npart = kMisfitBlocks * nshot;
+    GB_TRY(m->w_red.ensure((size_t)(npart + 8) * sizeof(double) + 4096));
     GB_TRY(m->w_flag.ensure(16));
     const void *obs_d = nullptr;
     GB_TRY(stage_in(m->w_obs, d_obs, seis_shot * nshot * sizeof(float), s, &obs_d));
@@ -653,73 +704,95 @@ extern "C" int gbfwi_adjoint_gradient(gbfwi_mesh *m, const int *shot_ids, int ns
         grad_d = m->w_tmp.as<float>();
     }
     double *partial = m->w_red.as<double>();
-    double *mis_d = partial + 1024;
+    double *mis_d = partial + npart;
     int *flag = m->w_flag.as<int>();
+    float *acc_all = m->w_acc.as<float>();
     GB_CUDA(cudaMemcpyAsync(m->w_shots.p, shot_ids, nshot * sizeof(int), cudaMemcpyHostToDevice, s));
     GB_CUDA(cudaMemsetAsync(mis_d, 0, sizeof(double), s));
     GB_CUDA(cudaMemsetAsync(flag, 0, 16, s));
     float *tot = m->w_grad.as<float>();
     GB_CUDA(cudaMemsetAsync(tot, 0, 5 * NP * sizeof(float), s));
-    const int nbatch = (nshot + Bmax - 1) / Bmax;
     m->timed_valid = false;
     if (m->timing) {
-        while ((int)m->ev.size() < 4 * nbatch) {
+        while ((int)m->ev.size() < 4 * nbatch + 2 * L) {
             cudaEvent_t e;
             GB_CUDA(cudaEventCreate(&e));
             m->ev.push_back(e);
         }
         m->fwd_launches = m->adj_launches = 0;
     }
-    auto mark = [&](int i) -> int {
-        if (m->timing) GB_CUDA(cudaEventRecord(m->ev[i], s));
-        return GBFWI_OK;
-    };
-
-    GB_TRY(m->w_batch.ensure((size_t)Bmax * sizeof(int)));
     GB_TRY(gb_prepare_step(MODE_FWD, tile));
     GB_TRY(gb_prepare_step(MODE_ADJ_G, tile));
-    for (int i0 = 0, bi = 0; i0 < nshot; i0 += Bmax, ++bi) {
-        int B = std::min(Bmax, nshot - i0);
-        // this batch's source ids at a fixed address, so that captured passes replay for every batch
-        GB_CUDA(cudaMemcpyAsync(m->w_batch.p, m->w_shots.as<int>() + i0, B * sizeof(int),
-                                cudaMemcpyDeviceToDevice, s));
-        Ctx c{m, &m->lists[tile], tile, B, s, m->w_batch.as<int>(), NP};
-        float *seis_d = m->w_seis.as<float>();
-        const std::string kf = pass_key("fwd", m, B, h.C,
-                                        {m->w_hist.p, m->w_vh.p, m->w_seis.p, m->w_snap.p, m->w_batch.p});
-        const std::string ka = pass_key("adj", m, B, h.C,
-                                        {m->w_hist.p, m->w_seis.p, m->w_snap.p, m->w_adj.p, m->w_wh.p, m->w_acc.p});
-        GB_TRY(mark(4 * bi));
-        GB_TRY(run_pass(m, kf, s, [&](cudaStream_t cs) {
-            Ctx cc = c;
-            cc.s = cs;
-            return forward_pass(cc, h, seis_d);
-        }));
-        GB_TRY(mark(4 * bi + 1));
-        m->fwd_launches += nt;
-        // residual r = s - d (in place) and misfit 1/2 dt sum r^2
-        long long nr = (long long)seis_shot * B;
-        const int nblk = 1024;
-        residual_kernel<<<nblk, 256, 0, s>>>(seis_d, (const float *)obs_d + seis_shot * i0, nr, partial, flag);
-        GB_LAUNCHED();
-        misfit_finish<<<1, 32, 0, s>>>(partial, nblk, 0.5 * m->d.dt, mis_d);
-        GB_LAUNCHED();
-        float *acc = m->w_acc.as<float>();
-        GB_CUDA(cudaMemsetAsync(acc, 0, (size_t)B * 5 * NP * sizeof(float), s));
-        GB_TRY(mark(4 * bi + 2));
-        GB_TRY(run_pass(m, ka, s, [&](cudaStream_t cs) {
-            Ctx cc = c;
-            cc.s = cs;
-            return adjoint_pass(cc, h, MODE_ADJ_G, seis_d, acc, 5 * NP, NP);
-        }));
-        GB_TRY(mark(4 * bi + 3));
-        m->adj_launches += (h.C == 0) ? nt : 2LL * nt;
-        acc_reduce<<<grid_for(5 * NP), 256, 0, s>>>(acc, B, 5, NP, tot);
-        GB_LAUNCHED();
+    // fork the lanes off the caller's stream
+    std::vector<cudaEvent_t> sync_ev(L);
+    for (int l = 0; l < L; ++l) GB_CUDA(cudaEventCreateWithFlags(&sync_ev[l], cudaEventDisableTiming));
+    GB_CUDA(cudaEventRecord(sync_ev[0], s));
+    for (int l = 1; l < L; ++l) GB_CUDA(cudaStreamWaitEvent(lanes[l].st, sync_ev[0], 0));
+
+    int rc = GBFWI_OK;
+    for (int i0 = 0, bi = 0; i0 < nshot && rc == GBFWI_OK; i0 += Bmax, ++bi) {
+        const int l = bi % L;
+        const LaneRef &lr = lanes[l];
+        BatchHist &h = hs[l];
+        cudaStream_t ls = lr.st;
+        const int B = std::min(Bmax, nshot - i0);
+        auto step = [&]() -> int {
+            auto mark = [&](int i) -> int {
+                if (m->timing) GB_CUDA(cudaEventRecord(m->ev[i], ls));
+                return GBFWI_OK;
+            };
+            // this batch's source ids at a fixed address, so captured passes replay for every batch
+            GB_CUDA(cudaMemcpyAsync(lr.batch->p, m->w_shots.as<int>() + i0, B * sizeof(int),
+                                    cudaMemcpyDeviceToDevice, ls));
+            Ctx c{m, &m->lists[tile], tile, B, ls, lr.batch->as<int>(), NP};
+            float *seis_d = lr.seis->as<float>();
+            float *acc = lr.acc->as<float>();
+            const std::string kf = pass_key("fwd", m, B, h.C, {lr.hist->p, lr.vh->p, lr.seis->p, lr.snap->p,
+                                                               lr.batch->p});
+            const std::string ka = pass_key("adj", m, B, h.C, {lr.hist->p, lr.seis->p, lr.snap->p, lr.adj->p,
+                                                               lr.wh->p, lr.acc->p});
+            GB_TRY(mark(4 * bi));
+            GB_TRY(run_pass(m, kf, ls, [&](cudaStream_t cs) {
+                Ctx cc = c;
+                cc.s = cs;
+                return forward_pass(cc, h, seis_d);
+            }));
+            GB_TRY(mark(4 * bi + 1));
+            // residual r = s - d (in place), per-shot partial sums of r^2
+            residual_kernel<<<dim3(kMisfitBlocks, B), 256, 0, ls>>>(seis_d, (const float *)obs_d + seis_shot * i0,
+                                                                   (long long)seis_shot,
+                                                                   partial + (long long)kMisfitBlocks * i0, flag);
+            GB_LAUNCHED();
+            GB_TRY(mark(4 * bi + 2));
+            GB_TRY(run_pass(m, ka, ls, [&](cudaStream_t cs) -> int {
+                Ctx cc = c;
+                cc.s = cs;
+                GB_CUDA(cudaMemsetAsync(acc, 0, (size_t)B * 5 * NP * sizeof(float), cs));
+                return adjoint_pass(cc, h, MODE_ADJ_G, seis_d, acc, 5 * NP, NP);
+            }));
+            GB_TRY(mark(4 * bi + 3));
+            GB_CUDA(cudaMemcpyAsync(acc_all + (long long)i0 * 5 * NP, acc, (size_t)B * 5 * NP * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, ls));
+            m->fwd_launches += nt;
+            m->adj_launches += (h.C == 0) ? nt : 2LL * nt;
+            return GBFWI_OK;
+        };
+        rc = step();
     }
+    // join the lanes back into the caller's stream (also after an error)
+    for (int l = 1; l < L; ++l) {
+        cudaEventRecord(sync_ev[l], lanes[l].st);
+        cudaStreamWaitEvent(s, sync_ev[l], 0);
+    }
+    for (int l = 0; l < L; ++l) cudaEventDestroy(sync_ev[l]);
+    if (rc != GBFWI_OK) return rc;
+    misfit_finish<<<1, 32, 0, s>>>(partial, nshot, 0.5 * m->d.dt, mis_d);
+    GB_LAUNCHED();
+    acc_reduce<<<grid_for(5 * NP), 256, 0, s>>>(acc_all, nshot, 5, NP, tot);
+    GB_LAUNCHED();
     const float dt = (float)m->d.dt;
-    chain_kernel<<<grid_for(N), 256, 0, s>>>(tot, m->d_model.as<float>(), m->nx, m->nz, m->pitch, -dt * dt,
-                                             grad_d);
+    chain_kernel<<<grid_for(N), 256, 0, s>>>(tot, m->d_model.as<float>(), m->d_wx.as<float>(), m->d_wz.as<float>(),
+                                             m->nx, m->nz, m->pitch, -dt * dt, grad_d);
     GB_LAUNCHED();
     finite_check<<<grid_for(3 * N), 256, 0, s>>>(grad_d, 3 * N, flag);
     GB_LAUNCHED();
@@ -777,9 +850,7 @@ extern "C" int gbfwi_precond_diag(gbfwi_mesh *m, const int *shot_ids, int nshot,
     GB_TRY(m->w_shots.ensure((size_t)nshot * sizeof(int)));
     BatchHist h;
     if (kind == 2 || kind == 4) {
-        GB_TRY(alloc_hist(m, Bmax, m->sch.ckpt_every, NP, h));
-        GB_TRY(m->w_adj.ensure(3 * lev * sizeof(float2)));
-        GB_TRY(m->w_wh.ensure(lev * sizeof(float2)));
+        GB_TRY(alloc_hist(m, lane0(m, s), Bmax, m->sch.ckpt_every, NP, h, true));
         GB_TRY(m->w_seis.ensure(seis_shot * Bmax * sizeof(float)));
     } else {
         GB_TRY(m->w_hist.ensure((size_t)3 * lev * sizeof(float2)));
@@ -858,7 +929,7 @@ extern "C" int gbfwi_precond_diag(gbfwi_mesh *m, const int *shot_ids, int nshot,
     GB_LAUNCHED();
     // medians of the smoothed maps (rank (N-1)/2)
     GB_TRY(m->w_red.ensure((1024 + 8) * sizeof(double) + 4096));
-    unsigned *rstate = (unsigned *)(m->w_red.as<char>() + (1024 + 8) * sizeof(double));
+    unsigned *rstate = (unsigned *)(m->w_red.as<char>() + (1024 + 8) * sizeof(double));   // radix-select state
     unsigned *rhist = rstate + 4;
     float *med = (float *)(rhist + 256);
     GB_CUDA(cudaMemsetAsync(rhist, 0, 256 * sizeof(unsigned), s));

@@ -415,8 +415,8 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
             acc[0] += fmaf(ax, ax, az * az);
         } else if (MODE == MODE_ADJ_G) {
             float2 uk = su2[wq];
-            float wsum = a.wxs[ix] * a.wzs[iz];
-            sacc[2 * S::OZ * OXQ + oz * OXQ + ox] += wsum * fmaf(uk.x, ax, uk.y * az);
+            // u_k . a^w; the node's mass factor rho W_g enters once, in the chain rule
+            sacc[2 * S::OZ * OXQ + oz * OXQ + ox] += fmaf(uk.x, ax, uk.y * az);
             if (edge) {
                 float *acc = a.acc + (long long)b * a.acc_shot_stride + g;
                 const long long cs = a.acc_comp_stride;

@@ -6,8 +6,9 @@ element mesh with all 24 shots in one launch and a shortened time axis:
   bitwise;
 * the gradient against central finite differences of the misfit with a
   relative step of 1e-3 along 20 seeded smooth perturbations (Gaussian bumps
-  on all three parameters).  The misfit is FP64-reduced from FP32
-  simulations, so the finite differences carry ~1e-3 relative noise.
+  on all three parameters): median relative error below 1e-2 and every
+  error below 1e-2 of the rms directional derivative (the misfit is
+  FP64-reduced from FP32 simulations).
 """
 import numpy as np
 import pytest
@@ -59,7 +60,7 @@ def test_autograd_gradient_against_finite_differences(setup):
     f.backward()
     g = [p.grad.double() for p in params]
     rng = np.random.default_rng(20)
-    errs = []
+    fds, ans = [], []
     eps = 1e-3
     for _ in range(20):
         dm = []
@@ -72,10 +73,13 @@ def test_autograd_gradient_against_finite_differences(setup):
                             m, ids, obs, 64).item()
             fm = fwi_misfit(*[(s.double() - eps * d).float().contiguous() for s, d in zip(start, dm)],
                             m, ids, obs, 64).item()
-        fd = (fp - fm) / (2 * eps)
-        an = float(sum((gc * d).sum() for gc, d in zip(g, dm)))
-        errs.append(abs(fd - an) / abs(an))
-    errs = np.array(errs)
-    print("FD relative errors: median %.2e max %.2e" % (np.median(errs), errs.max()))
-    assert np.median(errs) < 1e-2
-    assert errs.max() < 5e-2
+        fds.append((fp - fm) / (2 * eps))
+        ans.append(float(sum((gc * d).sum() for gc, d in zip(g, dm))))
+    fds, ans = np.array(fds), np.array(ans)
+    rel_err = np.abs(fds - ans) / np.abs(ans)
+    # directions whose derivative nearly cancels are judged against the
+    # typical derivative size instead of their own
+    scaled = np.abs(fds - ans) / np.sqrt(np.mean(ans ** 2))
+    print("FD: median relative error %.2e, max error / rms derivative %.2e" % (np.median(rel_err), scaled.max()))
+    assert np.median(rel_err) < 1e-2
+    assert scaled.max() < 1e-2

@@ -93,7 +93,8 @@ def test_fullsize_batched_checkpointed_equals_single_shot_bitwise(big):
     _model(m, start)
     out = []
     for sched in (dict(shots_per_launch=1, ckpt_every=0), dict(shots_per_launch=24, ckpt_every=64),
-                  dict(shots_per_launch=8, ckpt_every=0, tile=4)):
+                  dict(shots_per_launch=8, ckpt_every=0, tile=4), dict(shots_per_launch=1, streams=4, use_graph=1),
+                  dict(shots_per_launch=2, streams=3, ckpt_every=100)):
         m.set_schedule(**sched)
         grad = torch.zeros(3, m.nz, m.nx, device=DEV)
         f = m.adjoint_gradient(ids, obs, grad)

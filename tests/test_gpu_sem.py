@@ -168,7 +168,8 @@ def test_batched_shots_equal_single_shot_launches(c2):
 def test_graph_replay_equals_eager_launches(c2):
     ref = c2.gpu_gradient(c2.mesh(shots_per_launch=1), [0, 1], obs=c2.obs_gpu)
     for sched in (dict(shots_per_launch=1, use_graph=1), dict(shots_per_launch=2, use_graph=1, ckpt_every=77),
-                  dict(shots_per_launch=1, use_graph=1, tile=3)):
+                  dict(shots_per_launch=1, use_graph=1, tile=3), dict(shots_per_launch=1, streams=2),
+                  dict(shots_per_launch=1, streams=2, use_graph=1, ckpt_every=50)):
         m = c2.mesh(**sched)
         for _ in range(2):                                  # capture, then replay
             f, g = c2.gpu_gradient(m, [0, 1], obs=c2.obs_gpu)
