@@ -31,6 +31,8 @@
 
 void gb_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 void gb_note_launch();
+void gb_note_launches(long long n);        // kernels launched by a graph replay
+long long gb_launches_so_far();
 
 // after every kernel launch: count it and surface launch errors
 #define GB_LAUNCHED()                 \
@@ -136,7 +138,12 @@ struct gbfwi_mesh {
     std::vector<Lane *> lanes;
     // CUDA graphs of whole forward / adjoint passes, keyed by schedule,
     // batch size and work-buffer addresses
-    std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;
+    struct CachedGraph {
+        std::string key;
+        cudaGraphExec_t exec;
+        long long kernels;   // kernel launches recorded while capturing
+    };
+    std::vector<CachedGraph> graphs;
     cudaStream_t cap_stream = nullptr;
 
     // optional per-phase timing of adjoint_gradient

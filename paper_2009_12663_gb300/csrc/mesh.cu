@@ -24,13 +24,15 @@ static thread_local char g_err[512];
 static std::atomic<long long> g_launches{0};
 
 void gb_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void gb_note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long gb_launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 extern "C" long long gbfwi_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 gbfwi_mesh::~gbfwi_mesh()
 {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
-    for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+    for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (Lane *l : lanes) delete l;
 }

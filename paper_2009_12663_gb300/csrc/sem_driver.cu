@@ -599,8 +599,9 @@ int run_pass(gbfwi_mesh *m, const std::string &key, cudaStream_t s, const std::f
 {
     if (!m->sch.use_graph) return body(s);
     for (auto &g : m->graphs)
-        if (g.first == key) {
-            GB_CUDA(cudaGraphLaunch(g.second, s));
+        if (g.key == key) {
+            GB_CUDA(cudaGraphLaunch(g.exec, s));
+            gb_note_launches(g.kernels);
             return GBFWI_OK;
         }
     if (!m->cap_stream) GB_CUDA(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
@@ -611,10 +612,14 @@ int run_pass(gbfwi_mesh *m, const std::string &key, cudaStream_t s, const std::f
     GB_CUDA(cudaStreamWaitEvent(m->cap_stream, ready, 0));
     GB_CUDA(cudaEventDestroy(ready));
     GB_CUDA(cudaStreamSynchronize(m->cap_stream));
+    const long long before = gb_launches_so_far();
     GB_CUDA(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = body(m->cap_stream);
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(m->cap_stream, &graph);
+    // launches recorded during capture did not run: count them at replay
+    const long long kernels = gb_launches_so_far() - before;
+    gb_note_launches(-kernels);
     if (rc != GBFWI_OK || ce != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
         if (rc == GBFWI_OK) {
@@ -631,11 +636,12 @@ int run_pass(gbfwi_mesh *m, const std::string &key, cudaStream_t s, const std::f
         return GBFWI_ECUDA;
     }
     if (m->graphs.size() >= 16) {          // bounded cache
-        cudaGraphExecDestroy(m->graphs.front().second);
+        cudaGraphExecDestroy(m->graphs.front().exec);
         m->graphs.erase(m->graphs.begin());
     }
-    m->graphs.emplace_back(key, exec);
+    m->graphs.push_back({key, exec, kernels});
     GB_CUDA(cudaGraphLaunch(exec, s));
+    gb_note_launches(kernels);
     return GBFWI_OK;
 }
 

@@ -1,0 +1,48 @@
+"""The FWI driver around the C ABI (Algorithm 1 directions through the
+compact apply, Armijo steps) and the post-convergence uncertainty step."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+from paper_2009_12663_gb300 import experiments  # noqa: E402
+from paper_2009_12663_gb300.fwi import Problem, fwi, preconditioner  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def small():
+    return experiments.build(nex=40, nez=10, nshot=3, nt=900, f0=12.0)
+
+
+def test_bfgs_reduces_misfit_and_lbfgs_with_full_memory_is_bfgs(small):
+    mesh, ids, d_obs, true, start = small
+    prob = Problem(mesh, ids, d_obs)
+    _, h_full, store = fwi(prob, start, 4)
+    _, h_lbfgs, _ = fwi(prob, start, 4, memory=10)
+    rel = [h["rel_misfit"] for h in h_full]
+    assert rel[-1] < 0.9 * rel[0]
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(rel, rel[1:]))
+    assert [h["misfit"] for h in h_full] == [h["misfit"] for h in h_lbfgs]
+    assert store.count >= 2
+
+
+def test_p4_preconditioned_run_and_uncertainty_maps(small):
+    mesh, ids, d_obs, true, start = small
+    prob = Problem(mesh, ids, d_obs)
+    B0 = preconditioner(mesh, ids, start, 4, sigma=100.0)
+    assert torch.isfinite(B0).all() and (B0 > 0).all()
+    m, hist, store = fwi(prob, start, 4, B0=B0)
+    assert hist[-1]["rel_misfit"] < 0.9
+    k = store.count
+    p = r = k
+    V = torch.zeros(r, store.n, device=start.device)
+    lam = torch.zeros(r, dtype=torch.float64, device=start.device)
+    std = torch.zeros(store.n, device=start.device)
+    store.lowrank_invhess(p, r, seed=1, eps_prior=1.0, V=V, lam=lam, std=std)
+    s = std.cpu().numpy()
+    assert np.isfinite(s).all() and (s >= 0).all()
+    # with no data information the posterior std would be sqrt(B0); BFGS
+    # information lowers it on average (Eqs. 12-14)
+    b0 = B0[1:].reshape(-1).cpu().numpy()
+    assert s.mean() < np.sqrt(b0).mean()
