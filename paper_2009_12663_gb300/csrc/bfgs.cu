@@ -234,13 +234,28 @@ __global__ void middle_kernel(const double *__restrict__ T, const double *__rest
     }
 }
 
-// Cholesky G = R^T R (R upper, p x p, FP64, in global scratch), then
-// coef = R^-T (lower) as FP32 for the row combination Q = R^-T E.
-__global__ void chol_kernel(const double *__restrict__ G, int p, double *__restrict__ A, double *__restrict__ R,
-                            double *__restrict__ Rinv, float *__restrict__ coef, int *__restrict__ flag)
+// Cholesky G + shift tr(G) I = R^T R (R upper, p x p, FP64, in global
+// scratch), then coef = R^-T (lower) as FP32 for the row combination
+// Q = R^-T E.  shift = 0 is plain CholeskyQR; a small shift keeps the first
+// step of shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto &
+// Yanagisawa 2020) stable for ill-conditioned E.
+__global__ void chol_kernel(const double *__restrict__ G, int p, double shift, double *__restrict__ A,
+                            double *__restrict__ R, double *__restrict__ Rinv, float *__restrict__ coef,
+                            int *__restrict__ flag)
 {
     const int t = threadIdx.x, nt = blockDim.x;
-    for (int q = t; q < p * p; q += nt) { A[q] = G[q]; R[q] = 0.0; }
+    __shared__ double trace;
+    if (t == 0) {
+        double tr = 0.0;
+        for (int i = 0; i < p; ++i) tr += G[(long long)i * p + i];
+        trace = tr;
+    }
+    __syncthreads();
+    for (int q = t; q < p * p; q += nt) {
+        int i = q / p, j = q % p;
+        A[q] = G[q] + (i == j ? shift * trace : 0.0);
+        R[q] = 0.0;
+    }
     __syncthreads();
     __shared__ double piv;
     for (int j = 0; j < p; ++j) {
@@ -280,7 +295,7 @@ __global__ void chol_kernel(const double *__restrict__ G, int p, double *__restr
 // (round-robin pairs), eigenpairs ordered by |lambda| descending.
 // work: >= 4 p^2 + 4 p doubles; outputs lam[rank] FP64 and coef[rank][p] = U^T.
 __global__ void omega_eig_kernel(const double *__restrict__ R1, const double *__restrict__ R2,
-                                 const double *__restrict__ M1, int p, int rank, double *work,
+                                 const double *__restrict__ R3, const double *__restrict__ M1, int p, int rank, double *work,
                                  double *__restrict__ lam, float *__restrict__ coef, int *__restrict__ flag,
                                  int max_sweeps, int use_smem)
 {
@@ -293,11 +308,19 @@ __global__ void omega_eig_kernel(const double *__restrict__ R1, const double *__
     double *cs = U + (long long)p * p;      // [p] cos / sin pairs (2 per pair)
     __shared__ int piv_row;
     __shared__ double off_sh, tot_sh;
-    // Rt = R2 R1 ; Aug = [M1^T | Rt^T]
+    // Rt = R3 R2 R1 (upper triangular); Aug = [M1^T | Rt^T].  U (free until
+    // the eigen phase) holds R2 R1 first.
     for (int q = t; q < p * p; q += nt) {
         int i = q / p, j = q % p;
         double s = 0.0;
         for (int l = i; l <= j; ++l) s += R2[(long long)i * p + l] * R1[(long long)l * p + j];
+        U[q] = (j >= i) ? s : 0.0;
+    }
+    __syncthreads();
+    for (int q = t; q < p * p; q += nt) {
+        int i = q / p, j = q % p;
+        double s = 0.0;
+        for (int l = i; l <= j; ++l) s += R3[(long long)i * p + l] * U[(long long)l * p + j];
         Aug[(long long)j * 2 * p + p + i] = s;                    // Rt^T[j][i]
         Aug[(long long)i * 2 * p + j] = M1[(long long)j * p + i]; // M1^T[i][j]
     }
@@ -560,7 +583,7 @@ int reserve(gbfwi_bfgs *h, int p, bool lowrank)
     size_t ab = std::max<size_t>({(size_t)(h->k + 1) * 2, (size_t)std::max(h->k, 1) * p, (size_t)p * p});
     GB_TRY(h->part.ensure((size_t)(nsplit + 1) * ab * sizeof(double)));
     size_t pp = (size_t)p * p;
-    size_t sm = small_apply_doubles(h, p) + (lowrank ? pp * 10 + 8 * (size_t)p + 64 : 0);
+    size_t sm = small_apply_doubles(h, p) + (lowrank ? pp * 11 + 8 * (size_t)p + 64 : 0);
     sm = std::max(sm, (size_t)(4 * (h->k + 1) + 8));
     GB_TRY(h->small.ensure(sm * sizeof(double)));
     GB_TRY(h->coef.ensure(std::max<size_t>({pp, (size_t)p * 2 * std::max(h->k, 1), 16}) * sizeof(float)));
@@ -721,48 +744,55 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
     float *E = h->E.as<float>(), *Q = h->Q.as<float>();
     // 1. E = (B_{n+1} - B0) X
     GB_TRY(apply_dev(h, Xd, p, E, 1.0, 1, s));
-    // 2. CholeskyQR2: Q = R1^-T E, Q <- R2^-T Q
+    // 2. shifted CholeskyQR3: Q1 = R1^-T E (Gram shifted by 11 (n p + p (p+1)) u tr(G)),
+    //    then two plain CholeskyQR passes; E = Q R3 R2 R1 exactly by construction
     const size_t pp = (size_t)p * p;
-    double *G, *A, *R1, *R2, *Rinv, *M1, *work, *lam;
+    double *G, *A, *R1, *R2, *R3, *Rinv, *M1, *work, *lam;
     G = h->small.as<double>() + small_apply_doubles(h, p);
     A = G + pp;
     R1 = A + pp;
     R2 = R1 + pp;
-    Rinv = R2 + pp;
+    R3 = R2 + pp;
+    Rinv = R3 + pp;
     M1 = Rinv + pp;
     work = M1 + pp;          // 4 pp + 4 p
     lam = work + 4 * pp + 4 * (size_t)p;
     float *coef = h->coef.as<float>();
     int *flag = h->flag.as<int>();
     GB_CUDA(cudaMemsetAsync(flag, 0, 16, s));
+    const double shift = 11.0 * ((double)n * p + (double)p * (p + 1)) * 1.1102230246251565e-16;
     GB_TRY(atb(h, E, n, p, E, n, p, nullptr, G, p, s));
-    chol_kernel<<<1, 256, 0, s>>>(G, p, A, R1, Rinv, coef, flag);
+    chol_kernel<<<1, 256, 0, s>>>(G, p, shift, A, R1, Rinv, coef, flag);
     GB_LAUNCHED();
-    GB_TRY(combine(h, E, nullptr, p, p, coef, p, Q, nullptr, nullptr, 0.f, s));
+    GB_TRY(combine(h, E, nullptr, p, p, coef, p, Q, nullptr, nullptr, 0.f, s));   // Q1 in Q
     GB_TRY(atb(h, Q, n, p, Q, n, p, nullptr, G, p, s));
-    chol_kernel<<<1, 256, 0, s>>>(G, p, A, R2, Rinv, coef, flag);
+    chol_kernel<<<1, 256, 0, s>>>(G, p, 0.0, A, R2, Rinv, coef, flag);
     GB_LAUNCHED();
-    GB_TRY(combine(h, Q, nullptr, p, p, coef, p, E, nullptr, nullptr, 0.f, s));   // final Q in E
-    float *Qf = E;
-    // 3. M1 = Q^T X ; Omega (Q^T X) = R2 R1 ; eigenpairs
+    GB_TRY(combine(h, Q, nullptr, p, p, coef, p, E, nullptr, nullptr, 0.f, s));   // Q2 in E
+    GB_TRY(atb(h, E, n, p, E, n, p, nullptr, G, p, s));
+    chol_kernel<<<1, 256, 0, s>>>(G, p, 0.0, A, R3, Rinv, coef, flag);
+    GB_LAUNCHED();
+    GB_TRY(combine(h, E, nullptr, p, p, coef, p, Q, nullptr, nullptr, 0.f, s));   // Q3 in Q
+    float *Qf = Q;
+    // 3. M1 = Q^T X ; Omega (Q^T X) = R3 R2 R1 ; eigenpairs
     GB_TRY(atb(h, Qf, n, p, Xd, n, p, nullptr, M1, p, s));
     {
         const size_t ws = (4 * pp + 4 * (size_t)p) * sizeof(double);
         const int use_smem = ws <= 200 * 1024;
         if (use_smem)
             GB_CUDA(cudaFuncSetAttribute(omega_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
-        omega_eig_kernel<<<1, 512, use_smem ? ws : 0, s>>>(R1, R2, M1, p, rank, work, lam, coef, flag, 60,
+        omega_eig_kernel<<<1, 512, use_smem ? ws : 0, s>>>(R1, R2, R3, M1, p, rank, work, lam, coef, flag, 60,
                                                           use_smem);
         GB_LAUNCHED();
     }
     // 4. V = Q U (first `rank` columns)
     const bool devV = V && gb_is_device_ptr(V);
-    float *Vd = devV ? V : Q;     // Q buffer is free now
+    float *Vd = devV ? V : E;     // E buffer is free now
     GB_TRY(combine(h, Qf, nullptr, p, p, coef, rank, Vd, nullptr, nullptr, 0.f, s));
     // 5. posterior std (Eq. 14)
     if (std_out) {
         bool devS = gb_is_device_ptr(std_out);
-        float *Sd = devS ? std_out : Qf;   // E buffer free after V
+        float *Sd = devS ? std_out : (devV ? E : Qf);   // a buffer not holding V
         std_kernel<<<grid_n(n), 256, 0, s>>>(Vd, lam, rank, h->B0.as<float>(), n, (float)eps_prior, Sd);
         GB_LAUNCHED();
         if (!devS) GB_CUDA(cudaMemcpyAsync(std_out, Sd, n * sizeof(float), cudaMemcpyDeviceToHost, s));
