@@ -42,10 +42,32 @@ namespace {
 constexpr int AT = 64;          // output tile of the split-K product
 constexpr int KI = 32;          // i-chunk staged per step
 
+// One term of a compensated FP32 dot product (Ogita, Rump & Oishi 2005,
+// "Accurate sum and dot product", algorithm Dot2): the product is split
+// exactly into pr + pe with an FMA, the running sum hi + pr exactly into
+// s + se (Knuth's TwoSum), and the error terms are collected in lo.  The
+// _rn intrinsics keep the compiler from contracting the products into FMAs,
+// which would break the exact splits.  The result hi + lo is as accurate as
+// an FP64-accumulated sum of the FP32 products up to a term in n eps^2.
+__device__ __forceinline__ void dot2_term(float a, float b, float &hi, float &lo)
+{
+    const float pr = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -pr);
+    const float sm = __fadd_rn(hi, pr);
+    const float z = __fsub_rn(sm, hi);
+    const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(sm, z)), __fsub_rn(pr, z));
+    hi = sm;
+    lo = __fadd_rn(lo, __fadd_rn(se, pe));
+}
+
 // part[sx][a][b] = sum_{i in split sx} A[a][i] * w[i] * Bm[b][i]
 // Tiles of 64 rows x 32 columns of A and Bm are staged through two shared
 // buffers; the global loads of the next tile are issued before the current
-// tile is consumed.
+// tile is consumed.  ACC2 = false: plain FP32 accumulation within a split
+// (relative error ~1e-6, enough for the search direction); ACC2 = true:
+// compensated (Dot2) accumulation, for Gram matrices and projections of
+// ill-conditioned blocks in the randomized SVD.
+template <bool ACC2>
 __global__ void __launch_bounds__(256) atb_partial(const float *__restrict__ A, long long lda, int ka,
                                                    const float *__restrict__ Bm, long long ldb, int kb,
                                                    const float *__restrict__ w, long long n, long long chunk,
@@ -81,6 +103,7 @@ __global__ void __launch_bounds__(256) atb_partial(const float *__restrict__ A, 
         }
     };
     float acc[4][4] = {};
+    float lo[4][4] = {};
     int buf = 0;
     if (ib < ie) {
         fetch(ib);
@@ -98,7 +121,12 @@ __global__ void __launch_bounds__(256) atb_partial(const float *__restrict__ A, 
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+                for (int v = 0; v < 4; ++v) {
+                    if constexpr (ACC2)
+                        dot2_term(av[u], bv[v], acc[u][v], lo[u][v]);
+                    else
+                        acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+                }
         }
         if (more) stash(buf ^ 1);
         __syncthreads();
@@ -109,7 +137,7 @@ __global__ void __launch_bounds__(256) atb_partial(const float *__restrict__ A, 
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             int a = a0 + ty * 4 + u, b = b0 + tx * 4 + v;
-            if (a < ka && b < kb) part[((long long)sx * ka + a) * kb + b] = (double)acc[u][v];
+            if (a < ka && b < kb) part[((long long)sx * ka + a) * kb + b] = (double)acc[u][v] + (double)lo[u][v];
         }
 }
 
@@ -236,9 +264,7 @@ __global__ void middle_kernel(const double *__restrict__ T, const double *__rest
 
 // Cholesky G + shift tr(G) I = R^T R (R upper, p x p, FP64, in global
 // scratch), then coef = R^-T (lower) as FP32 for the row combination
-// Q = R^-T E.  shift = 0 is plain CholeskyQR; a small shift keeps the first
-// step of shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto &
-// Yanagisawa 2020) stable for ill-conditioned E.
+// Q = R^-T E (one CholeskyQR pass; shift = 0 unless a caller regularises).
 __global__ void chol_kernel(const double *__restrict__ G, int p, double shift, double *__restrict__ A,
                             double *__restrict__ R, double *__restrict__ Rinv, float *__restrict__ coef,
                             int *__restrict__ flag)
@@ -261,7 +287,7 @@ __global__ void chol_kernel(const double *__restrict__ G, int p, double shift, d
     for (int j = 0; j < p; ++j) {
         if (t == 0) {
             double dj = A[(long long)j * p + j];
-            if (!(dj > 0.0) || !isfinite(dj)) { *flag = 1; dj = 1.0; }
+            if (!(dj > 0.0) || !isfinite(dj)) { *flag = 2; dj = 1.0; }
             piv = sqrt(dj);
             R[(long long)j * p + j] = piv;
         }
@@ -290,170 +316,226 @@ __global__ void chol_kernel(const double *__restrict__ G, int p, double shift, d
     }
 }
 
-// Omega from Omega (Q^T X) = Q^T E with Q^T E = R2 R1 (CholeskyQR2), its
-// symmetric part's eigendecomposition by parallel cyclic Jacobi
-// (round-robin pairs), eigenpairs ordered by |lambda| descending.
-// work: >= 4 p^2 + 4 p doubles; outputs lam[rank] FP64 and coef[rank][p] = U^T.
-__global__ void omega_eig_kernel(const double *__restrict__ R1, const double *__restrict__ R2,
-                                 const double *__restrict__ R3, const double *__restrict__ M1, int p, int rank, double *work,
-                                 double *__restrict__ lam, float *__restrict__ coef, int *__restrict__ flag,
-                                 int max_sweeps, int use_smem)
+// Block-cooperative cyclic Jacobi for a symmetric p x p matrix A (row-major,
+// overwritten by its eigenvalues on the diagonal); U accumulates the
+// eigenvectors as columns (must hold I on entry).  Round-robin pairing gives
+// p/2 disjoint rotations per round.  A pair is rotated only while
+// |a_pq| > 1e-15 sqrt(|a_pp a_qq|) (the relative threshold of Demmel &
+// Veselic 1992, which also resolves small eigenvalues of a graded matrix)
+// and |a_pq| > 1e-16 |A|_F (below that an entry is FP64 rounding noise of
+// the largest eigenvalues); the sweeps stop after one without a rotation,
+// or after max_sweeps.  cs: scratch of >= p + 1 doubles.
+__device__ void block_jacobi(double *A, double *U, int p, double *cs, int max_sweeps)
 {
     const int t = threadIdx.x, nt = blockDim.x;
+    __shared__ int rotated;
+    __shared__ double fro;
+    const int P = (p + 1) & ~1;
+    const int npair = P / 2;
+    __syncthreads();
+    if (t == 0) fro = 0.0;
+    __syncthreads();
+    {
+        double f = 0.0;
+        for (int q = t; q < p * p; q += nt) f += A[q] * A[q];
+        atomicAdd(&fro, f);
+    }
+    __syncthreads();
+    const double abs_tol = 1e-16 * sqrt(fro);
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        __syncthreads();
+        if (t == 0) rotated = 0;
+        __syncthreads();
+        for (int round = 0; round < P - 1; ++round) {
+            for (int m = t; m < npair; m += nt) {
+                int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
+                int b = 1 + (P - 2 - m + round) % (P - 1);
+                double c = 1.0, sn = 0.0;
+                if (a < p && b < p) {
+                    int pp = min(a, b), qq = max(a, b);
+                    double apq = A[(long long)pp * p + qq];
+                    double app = A[(long long)pp * p + pp], aqq = A[(long long)qq * p + qq];
+                    if (fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && fabs(apq) > abs_tol) {
+                        double tau = (aqq - app) / (2.0 * apq);
+                        double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + tt * tt);
+                        sn = tt * c;
+                        rotated = 1;
+                    }
+                }
+                cs[2 * m] = c;
+                cs[2 * m + 1] = sn;
+            }
+            __syncthreads();
+            for (int q = t; q < npair * p; q += nt) {          // rows: A <- J^T A
+                int m = q / p, l = q % p;
+                int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
+                int b = 1 + (P - 2 - m + round) % (P - 1);
+                if (a >= p || b >= p || cs[2 * m + 1] == 0.0) continue;
+                int pp = min(a, b), qq = max(a, b);
+                double c = cs[2 * m], sn = cs[2 * m + 1];
+                double x = A[(long long)pp * p + l], y = A[(long long)qq * p + l];
+                A[(long long)pp * p + l] = c * x - sn * y;
+                A[(long long)qq * p + l] = sn * x + c * y;
+            }
+            __syncthreads();
+            for (int q = t; q < npair * p; q += nt) {          // columns: A <- A J, U <- U J
+                int m = q / p, l = q % p;
+                int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
+                int b = 1 + (P - 2 - m + round) % (P - 1);
+                if (a >= p || b >= p || cs[2 * m + 1] == 0.0) continue;
+                int pp = min(a, b), qq = max(a, b);
+                double c = cs[2 * m], sn = cs[2 * m + 1];
+                double x = A[(long long)l * p + pp], y = A[(long long)l * p + qq];
+                A[(long long)l * p + pp] = c * x - sn * y;
+                A[(long long)l * p + qq] = sn * x + c * y;
+                double u = U[(long long)l * p + pp], v = U[(long long)l * p + qq];
+                U[(long long)l * p + pp] = c * u - sn * v;
+                U[(long long)l * p + qq] = sn * u + c * v;
+            }
+            __syncthreads();
+        }
+        if (!rotated) break;
+    }
+    __syncthreads();
+}
+
+// Rank-revealing orthonormalisation of the probe block E [p][n] from its
+// FP64 Gram G = E E^T = W S^2 W^T: keep the r directions with singular value
+// >= tol * s_max and return coef [r][p] with Q1 = coef E = S_r^-1 W_r^T E;
+// *r_out = r.  An FP32 block carries ~1e-7 relative rounding, so directions
+// far below s_max are noise: combining them would amplify that rounding by
+// s_max / s_i, which is where plain CholeskyQR on E breaks down.
+__global__ void gram_basis_kernel(const double *__restrict__ G, int p, double tol, double *work,
+                                  float *__restrict__ coef, int *__restrict__ r_out, int *__restrict__ flag,
+                                  int use_smem)
+{
     extern __shared__ double smem_work[];
-    if (use_smem) work = smem_work;         // small p: the whole workspace in shared memory
-    double *Aug = work;                     // [p][2p]: [M1^T | Rt^T]
-    double *A = Aug + 2LL * p * p;          // [p][p] symmetric matrix
-    double *U = A + (long long)p * p;       // [p][p]
-    double *cs = U + (long long)p * p;      // [p] cos / sin pairs (2 per pair)
+    if (use_smem) work = smem_work;
+    const int t = threadIdx.x, nt = blockDim.x;
+    double *A = work, *U = A + (long long)p * p, *cs = U + (long long)p * p;
+    for (int q = t; q < p * p; q += nt) {
+        A[q] = G[q];
+        U[q] = (q / p == q % p) ? 1.0 : 0.0;
+    }
+    block_jacobi(A, U, p, cs, 60);
+    if (t == 0) {
+        int *used = reinterpret_cast<int *>(cs);
+        double smax = 0.0;
+        for (int i = 0; i < p; ++i) { used[i] = 0; smax = fmax(smax, A[(long long)i * p + i]); }
+        if (!(smax > 0.0) || !isfinite(smax)) *flag = 1;
+        int r = 0;
+        for (int c = 0; c < p; ++c) {
+            int best = -1;
+            double bv = -1.0;
+            for (int i = 0; i < p; ++i)
+                if (!used[i] && A[(long long)i * p + i] > bv) { bv = A[(long long)i * p + i]; best = i; }
+            if (best < 0 || !(bv > 0.0) || sqrt(bv) < tol * sqrt(smax)) break;
+            used[best] = 1;
+            const double inv = 1.0 / sqrt(bv);
+            for (int a = 0; a < p; ++a) coef[(long long)r * p + a] = (float)(U[(long long)a * p + best] * inv);
+            ++r;
+        }
+        *r_out = r;
+    }
+}
+
+// Single-pass randomized SVD core (Algorithm 3) with r <= p basis vectors:
+// Omega (Q^T X) = Q^T E solved in the least-squares sense,
+// Omega = QE QX^T (QX QX^T)^-1 (= QE QX^-1 when r = p), symmetrised, then
+// eigendecomposed; eigenpairs by |lambda| descending.  QE, QX: [r][p] FP64.
+// Outputs lam[rank] (zeros beyond r) and coef[rank][r] = U^T (zero rows
+// beyond r).  work: >= 4 r^2 + 4 r doubles (or shared memory).
+__global__ void omega_ls_kernel(const double *__restrict__ QE, const double *__restrict__ QX, int r, int p,
+                                int rank, double *work, double *__restrict__ lam, float *__restrict__ coef,
+                                int *__restrict__ flag, int use_smem)
+{
+    extern __shared__ double smem_work[];
+    if (use_smem) work = smem_work;
+    const int t = threadIdx.x, nt = blockDim.x;
+    double *Aug = work;                     // [r][2r]: [N | Bm^T], N = QX QX^T, Bm = QE QX^T
+    double *A = Aug + 2LL * r * r;          // [r][r]
+    double *U = A + (long long)r * r;       // [r][r]
+    double *cs = U + (long long)r * r;      // >= r + 1
     __shared__ int piv_row;
-    __shared__ double off_sh, tot_sh;
-    // Rt = R3 R2 R1 (upper triangular); Aug = [M1^T | Rt^T].  U (free until
-    // the eigen phase) holds R2 R1 first.
-    for (int q = t; q < p * p; q += nt) {
-        int i = q / p, j = q % p;
-        double s = 0.0;
-        for (int l = i; l <= j; ++l) s += R2[(long long)i * p + l] * R1[(long long)l * p + j];
-        U[q] = (j >= i) ? s : 0.0;
+    for (int q = t; q < r * r; q += nt) {
+        int i = q / r, j = q % r;
+        double nij = 0.0, bji = 0.0;
+        for (int c = 0; c < p; ++c) {
+            nij += QX[(long long)i * p + c] * QX[(long long)j * p + c];
+            bji += QE[(long long)j * p + c] * QX[(long long)i * p + c];   // Bm[j][i]
+        }
+        Aug[(long long)i * 2 * r + j] = nij;
+        Aug[(long long)i * 2 * r + r + j] = bji;                          // Bm^T[i][j]
     }
     __syncthreads();
-    for (int q = t; q < p * p; q += nt) {
-        int i = q / p, j = q % p;
-        double s = 0.0;
-        for (int l = i; l <= j; ++l) s += R3[(long long)i * p + l] * U[(long long)l * p + j];
-        Aug[(long long)j * 2 * p + p + i] = s;                    // Rt^T[j][i]
-        Aug[(long long)i * 2 * p + j] = M1[(long long)j * p + i]; // M1^T[i][j]
-    }
-    __syncthreads();
-    // Gauss-Jordan with partial pivoting: M1^T Omega^T = Rt^T
-    for (int j = 0; j < p; ++j) {
+    // Gauss-Jordan with partial pivoting: N Omega^T = Bm^T
+    for (int j = 0; j < r; ++j) {
         if (t == 0) {
             int best = j;
-            double bv = fabs(Aug[(long long)j * 2 * p + j]);
-            for (int r = j + 1; r < p; ++r) {
-                double v = fabs(Aug[(long long)r * 2 * p + j]);
-                if (v > bv) { bv = v; best = r; }
+            double bv = fabs(Aug[(long long)j * 2 * r + j]);
+            for (int rr = j + 1; rr < r; ++rr) {
+                double v = fabs(Aug[(long long)rr * 2 * r + j]);
+                if (v > bv) { bv = v; best = rr; }
             }
-            if (!(bv > 0.0)) *flag = 1;
+            if (!(bv > 0.0)) *flag = 3;
             piv_row = best;
         }
         __syncthreads();
         int pr = piv_row;
         if (pr != j)
-            for (int c = t; c < 2 * p; c += nt) {
-                double a = Aug[(long long)j * 2 * p + c];
-                Aug[(long long)j * 2 * p + c] = Aug[(long long)pr * 2 * p + c];
-                Aug[(long long)pr * 2 * p + c] = a;
+            for (int c = t; c < 2 * r; c += nt) {
+                double a = Aug[(long long)j * 2 * r + c];
+                Aug[(long long)j * 2 * r + c] = Aug[(long long)pr * 2 * r + c];
+                Aug[(long long)pr * 2 * r + c] = a;
             }
         __syncthreads();
-        double d = Aug[(long long)j * 2 * p + j];
+        double d = Aug[(long long)j * 2 * r + j];
         if (d == 0.0) d = 1.0;
         __syncthreads();
-        for (int c = t; c < 2 * p; c += nt) Aug[(long long)j * 2 * p + c] /= d;
+        for (int c = t; c < 2 * r; c += nt) Aug[(long long)j * 2 * r + c] /= d;
         __syncthreads();
-        for (int q = t; q < p * 2 * p; q += nt) {
-            int r = q / (2 * p), c = q % (2 * p);
-            if (r == j || c == j) continue;
-            Aug[(long long)r * 2 * p + c] -= Aug[(long long)r * 2 * p + j] * Aug[(long long)j * 2 * p + c];
+        for (int q = t; q < r * 2 * r; q += nt) {
+            int rr = q / (2 * r), c = q % (2 * r);
+            if (rr == j || c == j) continue;
+            Aug[(long long)rr * 2 * r + c] -= Aug[(long long)rr * 2 * r + j] * Aug[(long long)j * 2 * r + c];
         }
         __syncthreads();
-        for (int r = t; r < p; r += nt)
-            if (r != j) Aug[(long long)r * 2 * p + j] = 0.0;
+        for (int rr = t; rr < r; rr += nt)
+            if (rr != j) Aug[(long long)rr * 2 * r + j] = 0.0;
         __syncthreads();
     }
-    // Omega^T = Aug[:, p:];  A = (Omega + Omega^T) / 2,  U = I
-    for (int q = t; q < p * p; q += nt) {
-        int i = q / p, j = q % p;
-        double oij = Aug[(long long)j * 2 * p + p + i];   // Omega[i][j] = Omega^T[j][i]
-        double oji = Aug[(long long)i * 2 * p + p + j];
+    for (int q = t; q < r * r; q += nt) {
+        int i = q / r, j = q % r;
+        double oij = Aug[(long long)j * 2 * r + r + i];   // Omega[i][j] = Omega^T[j][i]
+        double oji = Aug[(long long)i * 2 * r + r + j];
         A[q] = 0.5 * (oij + oji);
         U[q] = (i == j) ? 1.0 : 0.0;
     }
-    __syncthreads();
-    const int P = (p + 1) & ~1;             // even number of slots (one dummy if p is odd)
-    const int npair = P / 2;
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        if (t == 0) { off_sh = 0.0; tot_sh = 0.0; }
-        __syncthreads();
-        double off = 0.0, tot = 0.0;
-        for (int q = t; q < p * p; q += nt) {
-            int i = q / p, j = q % p;
-            double v = A[q] * A[q];
-            tot += v;
-            if (i != j) off += v;
-        }
-        atomicAdd(&off_sh, off);
-        atomicAdd(&tot_sh, tot);
-        __syncthreads();
-        if (off_sh <= 1e-30 * tot_sh || off_sh == 0.0) break;
-        __syncthreads();
-        for (int round = 0; round < P - 1; ++round) {
-            // round-robin pairing: slot 0 fixed, slots 1..P-1 rotate
-            for (int m = t; m < npair; m += nt) {
-                int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
-                int b = 1 + (P - 2 - m + round) % (P - 1);
-                double c = 1.0, s = 0.0;
-                if (a < p && b < p) {
-                    int pp = min(a, b), qq = max(a, b);
-                    double apq = A[(long long)pp * p + qq];
-                    if (apq != 0.0) {
-                        double tau = (A[(long long)qq * p + qq] - A[(long long)pp * p + pp]) / (2.0 * apq);
-                        double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + tt * tt);
-                        s = tt * c;
-                    }
-                }
-                cs[2 * m] = c;
-                cs[2 * m + 1] = s;
-            }
-            __syncthreads();
-            // rows: A <- J^T A
-            for (int q = t; q < npair * p; q += nt) {
-                int m = q / p, l = q % p;
-                int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
-                int b = 1 + (P - 2 - m + round) % (P - 1);
-                if (a >= p || b >= p) continue;
-                int pp = min(a, b), qq = max(a, b);
-                double c = cs[2 * m], s = cs[2 * m + 1];
-                double x = A[(long long)pp * p + l], y = A[(long long)qq * p + l];
-                A[(long long)pp * p + l] = c * x - s * y;
-                A[(long long)qq * p + l] = s * x + c * y;
-            }
-            __syncthreads();
-            // columns: A <- A J, U <- U J
-            for (int q = t; q < npair * p; q += nt) {
-                int m = q / p, l = q % p;
-                int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
-                int b = 1 + (P - 2 - m + round) % (P - 1);
-                if (a >= p || b >= p) continue;
-                int pp = min(a, b), qq = max(a, b);
-                double c = cs[2 * m], s = cs[2 * m + 1];
-                double x = A[(long long)l * p + pp], y = A[(long long)l * p + qq];
-                A[(long long)l * p + pp] = c * x - s * y;
-                A[(long long)l * p + qq] = s * x + c * y;
-                double u = U[(long long)l * p + pp], v = U[(long long)l * p + qq];
-                U[(long long)l * p + pp] = c * u - s * v;
-                U[(long long)l * p + qq] = s * u + c * v;
-            }
-            __syncthreads();
-        }
-    }
-    __syncthreads();
+    block_jacobi(A, U, r, cs, 60);
     if (t == 0) {
-        // selection by |lambda| descending (stable: smaller index first on ties)
         int *used = reinterpret_cast<int *>(cs);
-        for (int i = 0; i < p; ++i) used[i] = 0;
-        for (int r = 0; r < rank; ++r) {
+        for (int i = 0; i < r; ++i) used[i] = 0;
+        for (int k = 0; k < rank; ++k) {
+            if (k >= r) {
+                lam[k] = 0.0;
+                for (int a2 = 0; a2 < r; ++a2) coef[(long long)k * r + a2] = 0.f;
+                continue;
+            }
             int best = -1;
             double bv = -1.0;
-            for (int i = 0; i < p; ++i) {
+            for (int i = 0; i < r; ++i) {
                 if (used[i]) continue;
-                double v = fabs(A[(long long)i * p + i]);
+                double v = fabs(A[(long long)i * r + i]);
                 if (v > bv) { bv = v; best = i; }
             }
+            if (best < 0) {                     // non-finite diagonal
+                *flag = 4;
+                for (best = 0; used[best]; ++best) {}
+            }
             used[best] = 1;
-            lam[r] = A[(long long)best * p + best];
-            for (int a2 = 0; a2 < p; ++a2) coef[(long long)r * p + a2] = (float)U[(long long)a2 * p + best];
+            lam[k] = A[(long long)best * r + best];
+            for (int a2 = 0; a2 < r; ++a2) coef[(long long)k * r + a2] = (float)U[(long long)a2 * r + best];
         }
     }
 }
@@ -514,7 +596,7 @@ int grid_n(long long n) { return (int)std::min<long long>(std::max<long long>((n
 
 // C[a][b] = sum_i A[a][i] w[i] Bm[b][i] -> out (device FP64, row stride ldo)
 int atb(gbfwi_bfgs *h, const float *A, long long lda, int ka, const float *Bm, long long ldb, int kb,
-        const float *w, double *out, long long ldo, cudaStream_t s)
+        const float *w, double *out, long long ldo, cudaStream_t s, bool accurate = false)
 {
     if (ka == 0 || kb == 0) return GBFWI_OK;
     const long long n = h->n;
@@ -523,7 +605,10 @@ int atb(gbfwi_bfgs *h, const float *A, long long lda, int ka, const float *Bm, l
     nsplit = (n + chunk - 1) / chunk;
     GB_TRY(h->part.ensure((size_t)nsplit * ka * kb * sizeof(double)));
     dim3 grid((unsigned)nsplit, (ka + AT - 1) / AT, (kb + AT - 1) / AT);
-    atb_partial<<<grid, 256, 0, s>>>(A, lda, ka, Bm, ldb, kb, w, n, chunk, h->part.as<double>());
+    if (accurate)
+        atb_partial<true><<<grid, 256, 0, s>>>(A, lda, ka, Bm, ldb, kb, w, n, chunk, h->part.as<double>());
+    else
+        atb_partial<false><<<grid, 256, 0, s>>>(A, lda, ka, Bm, ldb, kb, w, n, chunk, h->part.as<double>());
     GB_LAUNCHED();
     int nab = ka * kb;
     atb_reduce<<<(nab + 255) / 256, 256, 0, s>>>(h->part.as<double>(), (int)nsplit, nab, out, ldo, kb);
@@ -583,7 +668,7 @@ int reserve(gbfwi_bfgs *h, int p, bool lowrank)
     size_t ab = std::max<size_t>({(size_t)(h->k + 1) * 2, (size_t)std::max(h->k, 1) * p, (size_t)p * p});
     GB_TRY(h->part.ensure((size_t)(nsplit + 1) * ab * sizeof(double)));
     size_t pp = (size_t)p * p;
-    size_t sm = small_apply_doubles(h, p) + (lowrank ? pp * 11 + 8 * (size_t)p + 64 : 0);
+    size_t sm = small_apply_doubles(h, p) + (lowrank ? pp * 10 + 8 * (size_t)p + 64 : 0);
     sm = std::max(sm, (size_t)(4 * (h->k + 1) + 8));
     GB_TRY(h->small.ensure(sm * sizeof(double)));
     GB_TRY(h->coef.ensure(std::max<size_t>({pp, (size_t)p * 2 * std::max(h->k, 1), 16}) * sizeof(float)));
@@ -591,7 +676,8 @@ int reserve(gbfwi_bfgs *h, int p, bool lowrank)
 }
 
 // Z = (H - minus_B0 gamma B0) X into the device buffer Z ([p][n])
-int apply_dev(gbfwi_bfgs *h, const float *Xd, int p, float *Zd, double gamma, int minus_B0, cudaStream_t s)
+int apply_dev(gbfwi_bfgs *h, const float *Xd, int p, float *Zd, double gamma, int minus_B0, cudaStream_t s,
+              bool accurate = false)
 {
     const long long n = h->n;
     const int k = h->k;
@@ -605,8 +691,8 @@ int apply_dev(gbfwi_bfgs *h, const float *Xd, int p, float *Zd, double gamma, in
     }
     double *T = h->small.as<double>();
     double *scr = T + 2 * k * p;
-    GB_TRY(atb(h, h->S.as<float>(), n, k, Xd, n, p, nullptr, T, p, s));
-    GB_TRY(atb(h, h->BY.as<float>(), n, k, Xd, n, p, nullptr, T + (long long)k * p, p, s));
+    GB_TRY(atb(h, h->S.as<float>(), n, k, Xd, n, p, nullptr, T, p, s, accurate));
+    GB_TRY(atb(h, h->BY.as<float>(), n, k, Xd, n, p, nullptr, T + (long long)k * p, p, s, accurate));
     middle_kernel<<<(p + 63) / 64, 64, 0, s>>>(T, h->dSY.as<double>(), h->dYBY.as<double>(), k, h->kmax, p, gamma,
                                                scr, h->coef.as<float>());
     GB_LAUNCHED();
@@ -676,15 +762,15 @@ extern "C" int gbfwi_bfgs_update(gbfwi_bfgs *h, const float *s_, const float *y_
     double *d1 = h->small.as<double>();          // [(k+1)][2]
     double *d2 = d1 + 2 * (k + 1);               // [(k+1)]
     double *d3 = d2 + (k + 1);                   // [1]
-    GB_TRY(atb(h, h->S.as<float>(), n, k + 1, yk, n, 1, nullptr, d1, 2, s));
-    GB_TRY(atb(h, h->S.as<float>(), n, k + 1, sk, n, 1, nullptr, d1 + 1, 2, s));
-    GB_TRY(atb(h, h->BY.as<float>(), n, k + 1, yk, n, 1, nullptr, d2, 1, s));
-    GB_TRY(atb(h, yk, n, 1, yk, n, 1, nullptr, d3, 1, s));
+    GB_TRY(atb(h, h->S.as<float>(), n, k + 1, yk, n, 1, nullptr, d1, 2, s, true));
+    GB_TRY(atb(h, h->S.as<float>(), n, k + 1, sk, n, 1, nullptr, d1 + 1, 2, s, true));
+    GB_TRY(atb(h, h->BY.as<float>(), n, k + 1, yk, n, 1, nullptr, d2, 1, s, true));
+    GB_TRY(atb(h, yk, n, 1, yk, n, 1, nullptr, d3, 1, s, true));
     std::vector<double> hd(4 * (k + 1) + 1);
     GB_CUDA(cudaMemcpyAsync(hd.data(), d1, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     double ys = hd[2 * k], ss = hd[2 * k + 1], yy = hd[2 * (k + 1) + (k + 1)];
-    if (!std::isfinite(ys) || !std::isfinite(ss) || !std::isfinite(yy)) return GBFWI_ENONFINITE;
+    if (!std::isfinite(ys) || !std::isfinite(ss) || !std::isfinite(yy)) return gb_nonfinite("BFGS pair dot product");
     if (!(ys > 1e-12 * std::sqrt(ss) * std::sqrt(yy))) return GBFWI_ECURV;
     const int km = h->kmax;
     for (int i = 0; i <= k; ++i) {
@@ -743,56 +829,53 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
     GB_TRY(reserve(h, p, true));
     float *E = h->E.as<float>(), *Q = h->Q.as<float>();
     // 1. E = (B_{n+1} - B0) X
-    GB_TRY(apply_dev(h, Xd, p, E, 1.0, 1, s));
-    // 2. shifted CholeskyQR3: Q1 = R1^-T E (Gram shifted by 11 (n p + p (p+1)) u tr(G)),
-    //    then two plain CholeskyQR passes; E = Q R3 R2 R1 exactly by construction
+    GB_TRY(apply_dev(h, Xd, p, E, 1.0, 1, s, true));
+    // 2. rank-revealing basis of E: FP64 Gram eigendecomposition, directions
+    //    with relative singular value >= 1e-4 (resolved by an FP32 block),
+    //    then one CholeskyQR pass to restore orthonormality in FP32
     const size_t pp = (size_t)p * p;
-    double *G, *A, *R1, *R2, *R3, *Rinv, *M1, *work, *lam;
-    G = h->small.as<double>() + small_apply_doubles(h, p);
-    A = G + pp;
-    R1 = A + pp;
-    R2 = R1 + pp;
-    R3 = R2 + pp;
-    Rinv = R3 + pp;
-    M1 = Rinv + pp;
-    work = M1 + pp;          // 4 pp + 4 p
-    lam = work + 4 * pp + 4 * (size_t)p;
+    double *G = h->small.as<double>() + small_apply_doubles(h, p);
+    double *A = G + pp, *R2 = A + pp, *Rinv = R2 + pp, *QE = Rinv + pp, *QX = QE + pp;
+    double *work = QX + pp;               // 4 pp + 4 p
+    double *lam = work + 4 * pp + 4 * (size_t)p;
+    int *rdev = reinterpret_cast<int *>(lam + p + 2);
     float *coef = h->coef.as<float>();
     int *flag = h->flag.as<int>();
     GB_CUDA(cudaMemsetAsync(flag, 0, 16, s));
-    const double shift = 11.0 * ((double)n * p + (double)p * (p + 1)) * 1.1102230246251565e-16;
-    GB_TRY(atb(h, E, n, p, E, n, p, nullptr, G, p, s));
-    chol_kernel<<<1, 256, 0, s>>>(G, p, shift, A, R1, Rinv, coef, flag);
-    GB_LAUNCHED();
-    GB_TRY(combine(h, E, nullptr, p, p, coef, p, Q, nullptr, nullptr, 0.f, s));   // Q1 in Q
-    GB_TRY(atb(h, Q, n, p, Q, n, p, nullptr, G, p, s));
-    chol_kernel<<<1, 256, 0, s>>>(G, p, 0.0, A, R2, Rinv, coef, flag);
-    GB_LAUNCHED();
-    GB_TRY(combine(h, Q, nullptr, p, p, coef, p, E, nullptr, nullptr, 0.f, s));   // Q2 in E
-    GB_TRY(atb(h, E, n, p, E, n, p, nullptr, G, p, s));
-    chol_kernel<<<1, 256, 0, s>>>(G, p, 0.0, A, R3, Rinv, coef, flag);
-    GB_LAUNCHED();
-    GB_TRY(combine(h, E, nullptr, p, p, coef, p, Q, nullptr, nullptr, 0.f, s));   // Q3 in Q
-    float *Qf = Q;
-    // 3. M1 = Q^T X ; Omega (Q^T X) = R3 R2 R1 ; eigenpairs
-    GB_TRY(atb(h, Qf, n, p, Xd, n, p, nullptr, M1, p, s));
-    {
-        const size_t ws = (4 * pp + 4 * (size_t)p) * sizeof(double);
-        const int use_smem = ws <= 200 * 1024;
-        if (use_smem)
-            GB_CUDA(cudaFuncSetAttribute(omega_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
-        omega_eig_kernel<<<1, 512, use_smem ? ws : 0, s>>>(R1, R2, R3, M1, p, rank, work, lam, coef, flag, 60,
-                                                          use_smem);
-        GB_LAUNCHED();
+    const size_t ws = (4 * pp + 4 * (size_t)p) * sizeof(double);
+    const int use_smem = ws <= 200 * 1024;
+    if (use_smem) {
+        GB_CUDA(cudaFuncSetAttribute(gram_basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
+        GB_CUDA(cudaFuncSetAttribute(omega_ls_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
     }
-    // 4. V = Q U (first `rank` columns)
+    GB_TRY(atb(h, E, n, p, E, n, p, nullptr, G, p, s, true));
+    gram_basis_kernel<<<1, 512, use_smem ? ws : 0, s>>>(G, p, 1e-4, work, coef, rdev, flag, use_smem);
+    GB_LAUNCHED();
+    int r = 0;
+    GB_CUDA(cudaMemcpyAsync(&r, rdev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (r < 1) return gb_nonfinite("probe block E = (B - B0) X is zero or not finite");
+    GB_TRY(combine(h, E, nullptr, p, p, coef, r, Q, nullptr, nullptr, 0.f, s));   // Q1 [r][n] in Q
+    GB_TRY(atb(h, Q, n, r, Q, n, r, nullptr, G, r, s, true));
+    chol_kernel<<<1, 256, 0, s>>>(G, r, 0.0, A, R2, Rinv, coef, flag);
+    GB_LAUNCHED();
+    float *Qf = h->V.as<float>();
+    GB_TRY(h->V.ensure((size_t)p * n * sizeof(float)));
+    Qf = h->V.as<float>();
+    GB_TRY(combine(h, Q, nullptr, r, r, coef, r, Qf, nullptr, nullptr, 0.f, s));  // Q [r][n]
+    // 3. Q^T E, Q^T X ; Omega by least squares ; eigenpairs
+    GB_TRY(atb(h, Qf, n, r, E, n, p, nullptr, QE, p, s, true));
+    GB_TRY(atb(h, Qf, n, r, Xd, n, p, nullptr, QX, p, s, true));
+    omega_ls_kernel<<<1, 512, use_smem ? ws : 0, s>>>(QE, QX, r, p, rank, work, lam, coef, flag, use_smem);
+    GB_LAUNCHED();
+    // 4. V = Q U (first `rank` eigenvectors; rows beyond r are zero)
     const bool devV = V && gb_is_device_ptr(V);
     float *Vd = devV ? V : E;     // E buffer is free now
-    GB_TRY(combine(h, Qf, nullptr, p, p, coef, rank, Vd, nullptr, nullptr, 0.f, s));
+    GB_TRY(combine(h, Qf, nullptr, r, r, coef, rank, Vd, nullptr, nullptr, 0.f, s));
     // 5. posterior std (Eq. 14)
     if (std_out) {
         bool devS = gb_is_device_ptr(std_out);
-        float *Sd = devS ? std_out : (devV ? E : Qf);   // a buffer not holding V
+        float *Sd = devS ? std_out : Q;   // Q buffer is free now
         std_kernel<<<grid_n(n), 256, 0, s>>>(Vd, lam, rank, h->B0.as<float>(), n, (float)eps_prior, Sd);
         GB_LAUNCHED();
         if (!devS) GB_CUDA(cudaMemcpyAsync(std_out, Sd, n * sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -804,6 +887,10 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
     int flag_h = 0;
     GB_CUDA(cudaMemcpyAsync(&flag_h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
-    if (flag_h) return GBFWI_ENONFINITE;
+    if (flag_h) {
+        static const char *stage[] = {"", "Gram matrix of E", "Cholesky pivot of the basis Gram matrix",
+                                      "singular Q^T X", "eigenvalues of Omega"};
+        return gb_nonfinite(stage[flag_h >= 1 && flag_h <= 4 ? flag_h : 0]);
+    }
     return GBFWI_OK;
 }

@@ -30,6 +30,8 @@
     } while (0)
 
 void gb_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+// records what was non-finite (named by gbfwi_strerror) and returns GBFWI_ENONFINITE
+int gb_nonfinite(const char *what);
 void gb_note_launch();
 void gb_note_launches(long long n);        // kernels launched by a graph replay
 long long gb_launches_so_far();

@@ -21,6 +21,7 @@ int gb_upload_gll(const double *D, const double *w);
 // ---------------------------------------------------------------------------
 
 static thread_local char g_err[512];
+static thread_local char g_nonfinite[256];
 static std::atomic<long long> g_launches{0};
 
 void gb_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -58,6 +59,12 @@ extern "C" int gbfwi_last_phase_times(const gbfwi_mesh *m, double *fwd_ms, doubl
 void gb_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line)
 {
     snprintf(g_err, sizeof(g_err), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+}
+
+int gb_nonfinite(const char *what)
+{
+    snprintf(g_nonfinite, sizeof(g_nonfinite), "non-finite value: %s", what);
+    return GBFWI_ENONFINITE;
 }
 
 int DevBuf::ensure(size_t nbytes)
@@ -102,7 +109,7 @@ extern "C" const char *gbfwi_strerror(int code)
     case GBFWI_ECUDA: return g_err[0] ? g_err : "CUDA error";
     case GBFWI_ECFL: return "time step violates the stability bound dt*vp_max/dx_min <= 0.5";
     case GBFWI_ECURV: return "BFGS pair rejected (curvature y^T s <= 0)";
-    case GBFWI_ENONFINITE: return "non-finite value";
+    case GBFWI_ENONFINITE: return g_nonfinite[0] ? g_nonfinite : "non-finite value";
     case GBFWI_ETIMEOUT: return "device-side wait timed out";
     case GBFWI_ENOMODEL: return "no model set";
     case GBFWI_ESCRATCH: return "request exceeds the fixed scratch of a no-allocation entry point (at most 256 shots)";
@@ -545,7 +552,7 @@ extern "C" int gbfwi_set_model(gbfwi_mesh *m, const float *rho, const float *vp,
     double vmax = 0;
     for (size_t g = 0; g < N; ++g) {
         float r = h[g], p = h[N + g], q = h[2 * N + g];
-        if (!std::isfinite(r) || !std::isfinite(p) || !std::isfinite(q)) return GBFWI_ENONFINITE;
+        if (!std::isfinite(r) || !std::isfinite(p) || !std::isfinite(q)) return gb_nonfinite("model parameter");
         if (!(r > 0) || !(q > 0) || !(p > q)) return GBFWI_EINVAL;
         vmax = std::max(vmax, (double)p);
     }

@@ -110,7 +110,7 @@ extern "C" int gbfwi_misfit_noalloc(const float *syn, const float *obs, int nsho
     GB_CUDA(cudaMemcpyAsync(res, scratch + kMaxShots * kBlocksPerShot, nshot * sizeof(double),
                             cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
-    if (flag_h != 0) return GBFWI_ENONFINITE;
+    if (flag_h != 0) return gb_nonfinite("misfit");
     for (int i = 0; i < nshot; ++i) misfit[i] = res[i];
     return GBFWI_OK;
 }

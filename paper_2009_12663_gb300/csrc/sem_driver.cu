@@ -468,7 +468,7 @@ extern "C" int gbfwi_misfit(gbfwi_mesh *m, const int *shot_ids, int nshot, const
     GB_CUDA(cudaMemcpyAsync(&mis_h, mis_d, sizeof(double), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaMemcpyAsync(&flag_h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
-    if (flag_h || !std::isfinite(mis_h)) return GBFWI_ENONFINITE;
+    if (flag_h || !std::isfinite(mis_h)) return gb_nonfinite("misfit");
     *misfit = mis_h;
     return GBFWI_OK;
 }
@@ -820,7 +820,7 @@ extern "C" int gbfwi_adjoint_gradient(gbfwi_mesh *m, const int *shot_ids, int ns
         m->adj_ms = am;
         m->timed_valid = true;
     }
-    if (flag_h || !std::isfinite(mis_h)) return GBFWI_ENONFINITE;
+    if (flag_h || !std::isfinite(mis_h)) return gb_nonfinite("misfit");
     if (!dev_grad) {
         GB_CUDA(cudaMemcpyAsync(grad, grad_d, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s));
         GB_CUDA(cudaStreamSynchronize(s));

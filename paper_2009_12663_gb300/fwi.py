@@ -107,7 +107,10 @@ def fwi(problem: Problem, m0: torch.Tensor, iterations: int, B0=None, memory=Non
             alpha = step0 * float(m[mask.to(m.device)].abs().max()) / float(p.abs().max())
         else:
             s_last, y_last = pairs[-1]
-            gamma = float((s_last * y_last).sum() / (y_last * y_last).sum())
+            # gamma_k of Algorithm 1 weighted by the preconditioner: the paper's
+            # s^T y / y^T y when B0 = I; for a physically scaled B0 the
+            # weighted form keeps gamma_k B0 y = s in the mean (unit steps)
+            gamma = float((s_last * y_last).sum() / (y_last * b0 * y_last).sum())
             z = torch.zeros(1, n, device=m.device)
             cur.apply(gv[None].contiguous(), z, gamma=gamma, minus_B0=False)
             p = -z[0]

@@ -153,3 +153,24 @@ def test_lowrank_full_rank_equals_dense_inverse_hessian():
     assert rel(std.cpu().numpy(), np.sqrt(np.diag(Bd))) < 1e-4
     _, le = ob.exact_lowrank(S, Y, B0, rank)
     assert np.allclose(lam.cpu().numpy(), le, rtol=1e-4, atol=1e-6 * np.abs(le).max())
+
+
+def test_lowrank_rank_deficient_probe_block():
+    """p > 2k probes: E = (B_{n+1} - B0) X has rank 2k exactly, the other
+    p - 2k directions of the FP32 block are rounding noise.  The basis keeps
+    the 2k resolved directions: their eigenvalues equal the dense
+    eigendecomposition of B_{n+1} - B0 and the rest are returned as zero."""
+    n, k, p = 3675, 3, 11
+    b, S, Y, B0 = store(n, k)
+    X = synth.gaussian_block(9, p, n)
+    lam = torch.zeros(p, dtype=torch.float64, device=DEV)
+    V = torch.zeros(p, n, device=DEV)
+    std = torch.zeros(n, device=DEV)
+    b.lowrank_invhess(p, p, eps_prior=1.0, X=t32(X), V=V, lam=lam, std=std)
+    _, le = ob.exact_lowrank(S, Y, B0, 2 * k)
+    lg = lam.cpu().numpy()
+    assert np.allclose(lg[:2 * k], le, rtol=1e-4, atol=1e-6 * np.abs(le).max())
+    assert np.all(lg[2 * k:] == 0.0)
+    assert np.all(V.cpu().numpy()[2 * k:] == 0.0)
+    Bd = ob.dense_inverse(B0, S, Y)
+    assert rel(std.cpu().numpy(), np.sqrt(np.diag(Bd))) < 1e-4
