@@ -12,4 +12,7 @@ sem      spectral-element forward / adjoint / gradient / preconditioners (C, FP6
 bfgs     dense BFGS (Eq. 3), two-loop recursions (Algorithms 1 and 2),
          single-pass randomized SVD (Algorithm 3), posterior std (Eq. 14)
 philox   Philox4x32-10 counter-based generator (Salmon et al. 2011)
+unet     learned diagonal preconditioner: U-Net forward / backward, MSE, Adam,
+         bilinear node-grid <-> image resampling, input features (optional
+         bfloat16 rounding at the CUDA path's storage points)
 """
