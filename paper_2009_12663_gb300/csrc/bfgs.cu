@@ -762,10 +762,10 @@ extern "C" int gbfwi_bfgs_update(gbfwi_bfgs *h, const float *s_, const float *y_
     double *d1 = h->small.as<double>();          // [(k+1)][2]
     double *d2 = d1 + 2 * (k + 1);               // [(k+1)]
     double *d3 = d2 + (k + 1);                   // [1]
-    GB_TRY(atb(h, h->S.as<float>(), n, k + 1, yk, n, 1, nullptr, d1, 2, s, true));
-    GB_TRY(atb(h, h->S.as<float>(), n, k + 1, sk, n, 1, nullptr, d1 + 1, 2, s, true));
-    GB_TRY(atb(h, h->BY.as<float>(), n, k + 1, yk, n, 1, nullptr, d2, 1, s, true));
-    GB_TRY(atb(h, yk, n, 1, yk, n, 1, nullptr, d3, 1, s, true));
+    GB_TRY(atb(h, h->S.as<float>(), n, k + 1, yk, n, 1, nullptr, d1, 2, s));
+    GB_TRY(atb(h, h->S.as<float>(), n, k + 1, sk, n, 1, nullptr, d1 + 1, 2, s));
+    GB_TRY(atb(h, h->BY.as<float>(), n, k + 1, yk, n, 1, nullptr, d2, 1, s));
+    GB_TRY(atb(h, yk, n, 1, yk, n, 1, nullptr, d3, 1, s));
     std::vector<double> hd(4 * (k + 1) + 1);
     GB_CUDA(cudaMemcpyAsync(hd.data(), d1, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
@@ -829,7 +829,7 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
     GB_TRY(reserve(h, p, true));
     float *E = h->E.as<float>(), *Q = h->Q.as<float>();
     // 1. E = (B_{n+1} - B0) X
-    GB_TRY(apply_dev(h, Xd, p, E, 1.0, 1, s, true));
+    GB_TRY(apply_dev(h, Xd, p, E, 1.0, 1, s));
     // 2. rank-revealing basis of E: FP64 Gram eigendecomposition, directions
     //    with relative singular value >= 1e-4 (resolved by an FP32 block),
     //    then one CholeskyQR pass to restore orthonormality in FP32
