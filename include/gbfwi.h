@@ -226,6 +226,98 @@ int gbfwi_lowrank_invhess(gbfwi_bfgs *b, const float *X, int p, int rank,
 /* Free the store.  NULL is accepted. */
 int gbfwi_bfgs_destroy(gbfwi_bfgs *b);
 
+/* ------------------------------------------- learned preconditioner -- */
+
+/* A U-Net that predicts the logarithm of the raw diagonal pseudo-Hessian H
+ * (the P-maps of Eqs. 5-8 as returned by gbfwi_precond_diag) from five input
+ * channels on an image grid: vp / 4700, vs / 2700, rho / 2500 and the
+ * source-illumination and receiver-coverage masks (gbfwi_unet_features).
+ * The paper has no learned component: the network is the standard U-Net of
+ * Ronneberger, Fischer & Brox (2015) with `levels` levels of base * 2^l
+ * channels: per level two 3x3 convolutions with ReLU, 2x2 average pooling
+ * down, nearest 2x upsampling up with the skip connection concatenated after
+ * the upsampled features, and a 1x1 output convolution.  Weights and stored
+ * activations are bfloat16 (round to nearest even), every sum is FP32; the
+ * convolutions run as BF16 tensor-core GEMMs.  Its use: B0 of the BFGS from
+ * the predicted H through gbfwi_precond_from_hessian, with the computed map
+ * as the fallback (the decision is the caller's). */
+typedef struct gbfwi_unet gbfwi_unet;
+
+typedef struct {
+    int levels;     /* 1 .. 6 */
+    int base;       /* channels of level 0, a multiple of 8 */
+    int cin, cout;  /* input / output channels (5 and 3 for the preconditioner) */
+    int height;     /* image rows, a multiple of 2^(levels-1) */
+    int width;      /* image columns, a multiple of 8 * 2^(levels-1) */
+} gbfwi_unet_desc;
+
+/* Create a network with all parameters zero (set them with
+ * gbfwi_unet_set_params) and its activation buffers for one image.
+ * -> EINVAL, ENOMEM, ECUDA. */
+int gbfwi_unet_create(const gbfwi_unet_desc *desc, gbfwi_unet **out);
+
+/* Free the network.  NULL is accepted. */
+int gbfwi_unet_destroy(gbfwi_unet *net);
+
+/* Length of the flat FP32 parameter vector (padded layout below), or a
+ * negative code. */
+long long gbfwi_unet_num_params(const gbfwi_unet *net);
+
+/* Layer `layer` (parameter order: encoder levels 0..L-1 with two 3x3
+ * convolutions each, decoder levels L-2..0 with two each, the first on
+ * [upsampled, skip] channels, then the 1x1 output convolution):
+ * info[7] = {cout, cin, k, cout_pad, kc_pad, w_offset, b_offset}.  Its
+ * weights are the [cout_pad][kc_pad] block at w_offset of the flat vector,
+ * entry (o, c*k*k + ky*k + kx) for W[o][c][ky][kx], zero beyond cout and
+ * cin*k*k; its biases the cout_pad entries at b_offset.  layer < 0 returns
+ * the number of layers.  -> EINVAL. */
+int gbfwi_unet_layer_info(const gbfwi_unet *net, int layer, int *info);
+
+/* Copy the flat parameter vector in (resetting the Adam state) or out.
+ * Synchronise the stream.  -> EINVAL, ECUDA. */
+int gbfwi_unet_set_params(gbfwi_unet *net, const float *params, void *stream);
+int gbfwi_unet_get_params(const gbfwi_unet *net, float *params, void *stream);
+
+/* y [cout][height][width] (FP32) = U-Net(x [cin][height][width]).
+ * Synchronises the stream.  -> EINVAL, ENONFINITE, ECUDA. */
+int gbfwi_unet_forward(gbfwi_unet *net, const float *x, float *y, void *stream);
+
+/* Gradient of sum(dy * U-Net(x)) with respect to the flat parameter vector
+ * (padded entries are zero), for an output gradient dy [cout][height][width];
+ * grad: [num_params] FP32.  Synchronises the stream.  -> EINVAL, ECUDA. */
+int gbfwi_unet_gradient(gbfwi_unet *net, const float *x, const float *dy, float *grad, void *stream);
+
+/* One Adam step (Kingma & Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8, bias
+ * corrected) on the mean over `batch` samples of the mean squared error
+ * between U-Net(x_b) and target_b.  x: [batch][cin][height][width], target:
+ * [batch][cout][height][width]; *loss (host, may be NULL) = the batch mean
+ * of the losses before the step.  batch <= 1024.  Synchronises the stream.
+ * -> EINVAL, ENONFINITE, ECUDA. */
+int gbfwi_unet_train_step(gbfwi_unet *net, const float *x, const float *target, int batch, double lr,
+                          double *loss, void *stream);
+
+/* The five U-Net input channels [5][height][width] for the model (rho, vp,
+ * vs: [nz][nx]) on this mesh: vp / 4700, vs / 2700, rho / 2500 and the
+ * masks sum_s exp(-|x - x_s|^2 / 2 sigma^2) over the mesh's sources and over
+ * its receivers, each divided by its maximum, all bilinearly resampled from
+ * the node grid with corner nodes on corner pixels.  Synchronises the
+ * stream.  -> EINVAL, ENOMEM, ECUDA. */
+int gbfwi_unet_features(gbfwi_mesh *mesh, const float *rho, const float *vp, const float *vs, double sigma_m,
+                        int height, int width, float *x, void *stream);
+
+/* Bilinear resampling of device arrays [channels][sh][sw] onto
+ * [channels][dh][dw], corner samples aligned; op 1: interpolate log(max(v,
+ * 1e-30)); op 2: exponentiate the interpolated value.  -> EINVAL, ECUDA. */
+int gbfwi_resample(const float *src, int channels, int sh, int sw, float *dst, int dh, int dw, int op,
+                   void *stream);
+
+/* B0 [3][nz][nx] = 1 / (S(H) + damp_factor * median(S(H))) from a given
+ * raw map H [3][nz][nx] (for example a predicted one): the smoothing,
+ * damping and inversion of gbfwi_precond_diag.  Synchronises the stream.
+ * -> EINVAL, ECUDA, ENOMEM. */
+int gbfwi_precond_from_hessian(gbfwi_mesh *mesh, const float *H, double smooth_sigma_m, double damp_factor,
+                               float *B0, void *stream);
+
 /* -------------------------------------------------- without allocation -- */
 
 /* Per-shot misfit f_s = 1/2 dt sum |s - d|^2 of synthetics against observed

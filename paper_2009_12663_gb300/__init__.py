@@ -18,13 +18,13 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (ABI_SYMBOLS, GbfwiError, MeshDesc, Schedule, Source, check, lib, ptr,
+from ._lib import (ABI_SYMBOLS, GbfwiError, MeshDesc, Schedule, Source, UnetDesc, check, lib, ptr,
                    stream_of)
 
 __all__ = [
     "Mesh", "Bfgs", "GbfwiError", "ABI_SYMBOLS", "mesh_create", "set_model", "forward", "misfit",
     "adjoint_gradient", "precond_diag", "bfgs_create", "bfgs_update", "bfgs_apply",
-    "lowrank_invhess", "num_tiles", "tile_shape", "lib", "launch_count",
+    "lowrank_invhess", "num_tiles", "tile_shape", "lib", "launch_count", "Unet", "resample",
 ]
 
 F32, F64, I32 = np.float32, np.float64, np.int32
@@ -138,6 +138,19 @@ class Mesh:
                                        float(damp), ptr(H, F32), ptr(B0, F32), stream_of(H, B0)),
               "precond_diag")
 
+    def precond_from_hessian(self, H, sigma, damp, B0):
+        """B0 = 1 / (S(H) + damp median S(H)) from a given raw map H [3][nz][nx]."""
+        check(lib().gbfwi_precond_from_hessian(self._h, ptr(H, F32), float(sigma), float(damp), ptr(B0, F32),
+                                               stream_of(H, B0)), "precond_from_hessian")
+        return B0
+
+    def unet_features(self, rho, vp, vs, sigma, out):
+        """The five U-Net input channels [5][H][W] for this model and acquisition."""
+        check(lib().gbfwi_unet_features(self._h, ptr(rho, F32), ptr(vp, F32), ptr(vs, F32), float(sigma),
+                                        int(out.shape[1]), int(out.shape[2]), ptr(out, F32),
+                                        stream_of(rho, vp, vs, out)), "unet_features")
+        return out
+
 
 class Bfgs:
     """Handle of a full-history BFGS store (gbfwi_bfgs)."""
@@ -215,3 +228,72 @@ def bfgs_apply(b: Bfgs, X, Z, gamma=1.0, minus_B0=False):
 
 def lowrank_invhess(b: Bfgs, p, rank, seed=0, eps_prior=1.0, X=None, V=None, lam=None, std=None):
     return b.lowrank_invhess(p, rank, seed, eps_prior, X, V, lam, std)
+
+
+class Unet:
+    """Handle of the learned-preconditioner U-Net (gbfwi_unet): BF16
+    weights and activations, FP32 sums, tensor-core convolutions."""
+
+    def __init__(self, levels=4, base=32, cin=5, cout=3, height=256, width=1024):
+        d = UnetDesc(int(levels), int(base), int(cin), int(cout), int(height), int(width))
+        h_ = ctypes.c_void_p()
+        check(lib().gbfwi_unet_create(ctypes.byref(d), ctypes.byref(h_)), "unet_create")
+        self._h = h_
+        self.levels, self.base, self.cin, self.cout = int(levels), int(base), int(cin), int(cout)
+        self.height, self.width = int(height), int(width)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                lib().gbfwi_unet_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    @property
+    def num_params(self) -> int:
+        return check(lib().gbfwi_unet_num_params(self._h), "unet_num_params")
+
+    def layers(self):
+        """[(cout, cin, k, cout_pad, kc_pad, w_offset, b_offset)] in parameter order."""
+        n = check(lib().gbfwi_unet_layer_info(self._h, -1, None), "unet_layer_info")
+        out = []
+        for i in range(n):
+            info = np.zeros(7, I32)
+            check(lib().gbfwi_unet_layer_info(self._h, i, ptr(info, I32)), "unet_layer_info")
+            out.append(tuple(int(v) for v in info))
+        return out
+
+    def set_params(self, params):
+        check(lib().gbfwi_unet_set_params(self._h, ptr(params, F32), stream_of(params)), "unet_set_params")
+
+    def get_params(self, params):
+        check(lib().gbfwi_unet_get_params(self._h, ptr(params, F32), stream_of(params)), "unet_get_params")
+        return params
+
+    def forward(self, x, y):
+        check(lib().gbfwi_unet_forward(self._h, ptr(x, F32), ptr(y, F32), stream_of(x, y)), "unet_forward")
+        return y
+
+    def gradient(self, x, dy, grad):
+        check(lib().gbfwi_unet_gradient(self._h, ptr(x, F32), ptr(dy, F32), ptr(grad, F32),
+                                        stream_of(x, dy, grad)), "unet_gradient")
+        return grad
+
+    def train_step(self, x, target, lr) -> float:
+        batch = x.shape[0] if x.ndim == 4 else 1
+        loss = ctypes.c_double()
+        check(lib().gbfwi_unet_train_step(self._h, ptr(x, F32), ptr(target, F32), int(batch), float(lr),
+                                          ctypes.byref(loss), stream_of(x, target)), "unet_train_step")
+        return loss.value
+
+
+def resample(src, dst, op=0):
+    """Bilinear resampling of device arrays [C][sh][sw] -> [C][dh][dw]
+    (corners aligned); op 1: of log(src), op 2: exp of the result."""
+    C, sh, sw = src.shape
+    _, dh, dw = dst.shape
+    check(lib().gbfwi_resample(ptr(src, F32), int(C), int(sh), int(sw), ptr(dst, F32), int(dh), int(dw), int(op),
+                               stream_of(src, dst)), "resample")
+    return dst

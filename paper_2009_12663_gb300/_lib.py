@@ -30,6 +30,9 @@ ABI_SYMBOLS = (
     "gbfwi_bfgs_create", "gbfwi_bfgs_update", "gbfwi_bfgs_count", "gbfwi_bfgs_apply",
     "gbfwi_lowrank_invhess", "gbfwi_bfgs_destroy", "gbfwi_launch_count", "gbfwi_enable_timing",
     "gbfwi_last_phase_times", "gbfwi_misfit_noalloc", "gbfwi_strerror",
+    "gbfwi_unet_create", "gbfwi_unet_destroy", "gbfwi_unet_num_params", "gbfwi_unet_layer_info",
+    "gbfwi_unet_set_params", "gbfwi_unet_get_params", "gbfwi_unet_forward", "gbfwi_unet_gradient",
+    "gbfwi_unet_train_step", "gbfwi_unet_features", "gbfwi_resample", "gbfwi_precond_from_hessian",
 )
 
 
@@ -49,6 +52,11 @@ class MeshDesc(ctypes.Structure):
 class Source(ctypes.Structure):
     _fields_ = [("x", ctypes.c_double), ("z", ctypes.c_double), ("type", ctypes.c_int),
                 ("f0", ctypes.c_double), ("t0", ctypes.c_double), ("amp", ctypes.c_double)]
+
+
+class UnetDesc(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("base", ctypes.c_int), ("cin", ctypes.c_int), ("cout", ctypes.c_int),
+                ("height", ctypes.c_int), ("width", ctypes.c_int)]
 
 
 class Schedule(ctypes.Structure):
@@ -98,6 +106,21 @@ def lib(path: str | None = None):
         L.gbfwi_enable_timing.argtypes = [vp, ctypes.c_int]
         L.gbfwi_last_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+        L.gbfwi_unet_create.argtypes = [ctypes.POINTER(UnetDesc), ctypes.POINTER(vp)]
+        L.gbfwi_unet_destroy.argtypes = [vp]
+        L.gbfwi_unet_num_params.restype = ctypes.c_longlong
+        L.gbfwi_unet_num_params.argtypes = [vp]
+        L.gbfwi_unet_layer_info.argtypes = [vp, ctypes.c_int, vp]
+        L.gbfwi_unet_set_params.argtypes = [vp, vp, vp]
+        L.gbfwi_unet_get_params.argtypes = [vp, vp, vp]
+        L.gbfwi_unet_forward.argtypes = [vp, vp, vp, vp]
+        L.gbfwi_unet_gradient.argtypes = [vp, vp, vp, vp, vp]
+        L.gbfwi_unet_train_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_double), vp]
+        L.gbfwi_unet_features.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, vp]
+        L.gbfwi_resample.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, vp]
+        L.gbfwi_precond_from_hessian.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, vp, vp]
     return _LIB
 
 

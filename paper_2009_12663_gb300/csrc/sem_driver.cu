@@ -833,6 +833,70 @@ extern "C" int gbfwi_adjoint_gradient(gbfwi_mesh *m, const int *shot_ids, int ns
 // preconditioners P1..P4, smoothing, damping, inversion
 // ---------------------------------------------------------------------------
 
+// B0 = 1 / (S(H) + damp * median(S(H))) per parameter from the raw map Hd
+// [3][N] (device); S1, S2 scratch [3][N].  Writes B0 (device or host).
+static int b0_from_map(gbfwi_mesh *m, const float *Hd, float *S1, float *S2, double sigma, double damp, float *B0,
+                       cudaStream_t s)
+{
+    const long long N = (long long)m->nx * m->nz;
+    // smoothing tables (node coordinates along each axis, 5-sigma index ranges)
+    std::vector<float> cx(m->nx), cz(m->nz);
+    std::vector<int2> rx(m->nx), rz(m->nz);
+    {
+        std::vector<double> X((size_t)m->nx * m->nz), Z((size_t)m->nx * m->nz);
+        gbfwi_node_coords(m, X.data(), Z.data());
+        for (int i = 0; i < m->nx; ++i) cx[i] = (float)X[i];
+        for (int i = 0; i < m->nz; ++i) cz[i] = (float)Z[(size_t)i * m->nx];
+        auto ranges = [&](const std::vector<float> &c, std::vector<int2> &r) {
+            int n = (int)c.size();
+            for (int i = 0; i < n; ++i) {
+                int lo = i, hi = i;
+                while (lo > 0 && c[i] - c[lo - 1] <= 5.0 * sigma) --lo;
+                while (hi < n - 1 && c[hi + 1] - c[i] <= 5.0 * sigma) ++hi;
+                r[i] = make_int2(lo, hi);
+            }
+        };
+        ranges(cx, rx);
+        ranges(cz, rz);
+    }
+    std::vector<float> wxf(m->wx1.begin(), m->wx1.end()), wzf(m->wz1.begin(), m->wz1.end());
+    GB_TRY(m->w_stage.ensure((size_t)(m->nx + m->nz) * (2 * sizeof(float) + sizeof(int2)) + 64));
+    char *tb = m->w_stage.as<char>();
+    float *dcx = (float *)tb, *dcz = dcx + m->nx, *dwx = dcz + m->nz, *dwz = dwx + m->nx;
+    int2 *drx = (int2 *)(((uintptr_t)(dwz + m->nz) + 15) & ~(uintptr_t)15), *drz = drx + m->nx;
+    GB_CUDA(cudaMemcpyAsync(dcx, cx.data(), m->nx * sizeof(float), cudaMemcpyHostToDevice, s));
+    GB_CUDA(cudaMemcpyAsync(dcz, cz.data(), m->nz * sizeof(float), cudaMemcpyHostToDevice, s));
+    GB_CUDA(cudaMemcpyAsync(dwx, wxf.data(), m->nx * sizeof(float), cudaMemcpyHostToDevice, s));
+    GB_CUDA(cudaMemcpyAsync(dwz, wzf.data(), m->nz * sizeof(float), cudaMemcpyHostToDevice, s));
+    GB_CUDA(cudaMemcpyAsync(drx, rx.data(), m->nx * sizeof(int2), cudaMemcpyHostToDevice, s));
+    GB_CUDA(cudaMemcpyAsync(drz, rz.data(), m->nz * sizeof(int2), cudaMemcpyHostToDevice, s));
+    float inv2s2 = (float)(1.0 / (2.0 * sigma * sigma));
+    smooth_axis<<<grid_for(3 * N), 256, 0, s>>>(Hd, S1, m->nx, m->nz, 0, dcx, dwx, drx, inv2s2);
+    GB_LAUNCHED();
+    smooth_axis<<<grid_for(3 * N), 256, 0, s>>>(S1, S2, m->nx, m->nz, 1, dcz, dwz, drz, inv2s2);
+    GB_LAUNCHED();
+    // medians of the smoothed maps (rank (N-1)/2)
+    GB_TRY(m->w_red.ensure((1024 + 8) * sizeof(double) + 4096));
+    unsigned *rstate = (unsigned *)(m->w_red.as<char>() + (1024 + 8) * sizeof(double));   // radix-select state
+    unsigned *rhist = rstate + 4;
+    float *med = (float *)(rhist + 256);
+    GB_CUDA(cudaMemsetAsync(rhist, 0, 256 * sizeof(unsigned), s));
+    for (int c = 0; c < 3; ++c) {
+        radix_init<<<1, 32, 0, s>>>(rstate, (unsigned)((N - 1) / 2));
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            radix_hist<<<grid_for(N), 256, 0, s>>>(S2 + c * N, N, rstate, shift, rhist);
+            radix_pick<<<1, 32, 0, s>>>(rstate, rhist, shift, med + c);
+        }
+        GB_LAUNCHED();
+    }
+    const bool dev_b0 = gb_is_device_ptr(B0);
+    float *B0d = dev_b0 ? B0 : S1;   // S1 is free after the second pass
+    b0_kernel<<<grid_for(3 * N), 256, 0, s>>>(S2, med, N, (float)damp, B0d);
+    GB_LAUNCHED();
+    if (!dev_b0) GB_CUDA(cudaMemcpyAsync(B0, B0d, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    return GBFWI_OK;
+}
+
 extern "C" int gbfwi_precond_diag(gbfwi_mesh *m, const int *shot_ids, int nshot, int kind, double sigma,
                                   double damp, float *H, float *B0, void *stream)
 {
@@ -897,68 +961,28 @@ extern "C" int gbfwi_precond_diag(gbfwi_mesh *m, const int *shot_ids, int nshot,
                                                m->d_wz.as<float>(), m->nx, m->nz, m->pitch, kind, f0, f1, Hd);
     GB_LAUNCHED();
 
-    // smoothing tables (node coordinates along each axis, 5-sigma index ranges)
-    std::vector<float> cx(m->nx), cz(m->nz);
-    std::vector<int2> rx(m->nx), rz(m->nz);
-    {
-        std::vector<double> X((size_t)m->nx * m->nz), Z((size_t)m->nx * m->nz);
-        gbfwi_node_coords(m, X.data(), Z.data());
-        for (int i = 0; i < m->nx; ++i) cx[i] = (float)X[i];
-        for (int i = 0; i < m->nz; ++i) cz[i] = (float)Z[(size_t)i * m->nx];
-        auto ranges = [&](const std::vector<float> &c, std::vector<int2> &r) {
-            int n = (int)c.size();
-            for (int i = 0; i < n; ++i) {
-                int lo = i, hi = i;
-                while (lo > 0 && c[i] - c[lo - 1] <= 5.0 * sigma) --lo;
-                while (hi < n - 1 && c[hi + 1] - c[i] <= 5.0 * sigma) ++hi;
-                r[i] = make_int2(lo, hi);
-            }
-        };
-        ranges(cx, rx);
-        ranges(cz, rz);
-    }
-    std::vector<float> wxf(m->wx1.begin(), m->wx1.end()), wzf(m->wz1.begin(), m->wz1.end());
-    GB_TRY(m->w_stage.ensure((size_t)(m->nx + m->nz) * (2 * sizeof(float) + sizeof(int2)) + 64));
-    char *tb = m->w_stage.as<char>();
-    float *dcx = (float *)tb, *dcz = dcx + m->nx, *dwx = dcz + m->nz, *dwz = dwx + m->nx;
-    int2 *drx = (int2 *)(((uintptr_t)(dwz + m->nz) + 15) & ~(uintptr_t)15), *drz = drx + m->nx;
-    GB_CUDA(cudaMemcpyAsync(dcx, cx.data(), m->nx * sizeof(float), cudaMemcpyHostToDevice, s));
-    GB_CUDA(cudaMemcpyAsync(dcz, cz.data(), m->nz * sizeof(float), cudaMemcpyHostToDevice, s));
-    GB_CUDA(cudaMemcpyAsync(dwx, wxf.data(), m->nx * sizeof(float), cudaMemcpyHostToDevice, s));
-    GB_CUDA(cudaMemcpyAsync(dwz, wzf.data(), m->nz * sizeof(float), cudaMemcpyHostToDevice, s));
-    GB_CUDA(cudaMemcpyAsync(drx, rx.data(), m->nx * sizeof(int2), cudaMemcpyHostToDevice, s));
-    GB_CUDA(cudaMemcpyAsync(drz, rz.data(), m->nz * sizeof(int2), cudaMemcpyHostToDevice, s));
-    float inv2s2 = (float)(1.0 / (2.0 * sigma * sigma));
-    smooth_axis<<<grid_for(3 * N), 256, 0, s>>>(Hd, S1, m->nx, m->nz, 0, dcx, dwx, drx, inv2s2);
-    GB_LAUNCHED();
-    smooth_axis<<<grid_for(3 * N), 256, 0, s>>>(S1, S2, m->nx, m->nz, 1, dcz, dwz, drz, inv2s2);
-    GB_LAUNCHED();
-    // medians of the smoothed maps (rank (N-1)/2)
-    GB_TRY(m->w_red.ensure((1024 + 8) * sizeof(double) + 4096));
-    unsigned *rstate = (unsigned *)(m->w_red.as<char>() + (1024 + 8) * sizeof(double));   // radix-select state
-    unsigned *rhist = rstate + 4;
-    float *med = (float *)(rhist + 256);
-    GB_CUDA(cudaMemsetAsync(rhist, 0, 256 * sizeof(unsigned), s));
-    for (int c = 0; c < 3; ++c) {
-        radix_init<<<1, 32, 0, s>>>(rstate, (unsigned)((N - 1) / 2));
-        for (int shift = 24; shift >= 0; shift -= 8) {
-            radix_hist<<<grid_for(N), 256, 0, s>>>(S2 + c * N, N, rstate, shift, rhist);
-            radix_pick<<<1, 32, 0, s>>>(rstate, rhist, shift, med + c);
-        }
-        GB_LAUNCHED();
-    }
-    const bool dev_b0 = gb_is_device_ptr(B0);
-    GB_TRY(m->w_stage.ensure(m->w_stage.bytes));
-    float *B0d = dev_b0 ? B0 : S1;   // S1 is free after the second pass
-    b0_kernel<<<grid_for(3 * N), 256, 0, s>>>(S2, med, N, (float)damp, B0d);
-    GB_LAUNCHED();
-    if (!dev_b0) GB_CUDA(cudaMemcpyAsync(B0, B0d, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    GB_TRY(b0_from_map(m, Hd, S1, S2, sigma, damp, B0, s));
     if (H) {
         if (gb_is_device_ptr(H))
             GB_CUDA(cudaMemcpyAsync(H, Hd, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, s));
         else
             GB_CUDA(cudaMemcpyAsync(H, Hd, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s));
     }
+    GB_CUDA(cudaStreamSynchronize(s));
+    return GBFWI_OK;
+}
+
+extern "C" int gbfwi_precond_from_hessian(gbfwi_mesh *m, const float *H, double sigma, double damp, float *B0,
+                                          void *stream)
+{
+    if (!m || !H || !B0 || !(sigma > 0) || !(damp >= 0)) return GBFWI_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long N = (long long)m->nx * m->nz;
+    GB_TRY(m->w_tmp.ensure((size_t)9 * N * sizeof(float) + 4096));
+    float *Hd = m->w_tmp.as<float>();
+    float *S1 = Hd + 3 * N, *S2 = Hd + 6 * N;
+    GB_CUDA(cudaMemcpyAsync(Hd, H, 3 * N * sizeof(float), cudaMemcpyDefault, s));
+    GB_TRY(b0_from_map(m, Hd, S1, S2, sigma, damp, B0, s));
     GB_CUDA(cudaStreamSynchronize(s));
     return GBFWI_OK;
 }

@@ -1,0 +1,193 @@
+"""GPU parity of the learned-preconditioner U-Net (BF16 tensor-core
+convolutions) against the FP64 oracle with bfloat16 rounding at the same
+storage points, through the C ABI.
+
+Tolerances come from the arithmetic.  The two sides differ only by the
+order of the sums (FP32 on the GPU, FP64 in the oracle); as long as no
+stored bfloat16 value rounds differently they agree to FP32 noise, and the
+small networks (few layers, few channels) stay in that regime: relative L2
+5e-3 on the output, 2e-2 on each layer's gradient.  Once one stored value
+rounds the other way (one 2^-8 step) the difference cascades through the
+following bfloat16 stores and ReLU masks.  Perturbing every convolution sum
+of the oracle by 1e-7 relative (below the GPU's FP32 summation noise)
+measures that floor on these very networks: 0.8-0.9e-2 on the output of the
+4-level, 32-channel network, 5-7e-2 on the whole gradient vector (cosine
+0.997-0.999) and up to 0.13 on a single layer of the 4-level, 16-channel
+one.  The large cases therefore assert 2e-2 (output), 0.15 / cosine 0.99
+(whole gradient) and 0.3 (any layer): a wrong index, operand or layout
+gives O(1) errors."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import unet as ou
+
+torch = pytest.importorskip("torch")
+import paper_2009_12663_gb300 as gb  # noqa: E402
+from paper_2009_12663_gb300 import learned  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def setup_net(levels, base, H, W, seed):
+    net = gb.Unet(levels=levels, base=base, cin=5, cout=3, height=H, width=W)
+    rng = np.random.default_rng(seed)
+    params = ou.init_params(levels, base, 5, 3, seed)
+    params = [(Wt, rng.standard_normal(b.shape) * 0.05) for Wt, b in params]
+    flat = learned.pack(net.layers(), params)
+    net.set_params(torch.tensor(flat, device=DEV))
+    # the oracle sees the FP32 master weights the GPU rounds to bf16
+    params32 = learned.unpack(net.layers(), flat)
+    x = rng.standard_normal((5, H, W)).astype(np.float32)
+    return net, params32, x
+
+
+def test_layer_layout_matches_oracle_shapes():
+    net = gb.Unet(levels=4, base=32, cin=5, cout=3, height=32, width=256)
+    shapes = [(c, i, k) for c, i, k, *_ in net.layers()]
+    assert shapes == ou.layer_shapes(4, 32, 5, 3)
+    flat = learned.he_init(net, 1)
+    assert flat.size == net.num_params
+    back = learned.unpack(net.layers(), flat)
+    assert np.array_equal(learned.pack(net.layers(), back), flat)
+
+
+@pytest.mark.parametrize("levels,base,H,W,tol", [(1, 8, 8, 64, 5e-3), (3, 8, 16, 64, 5e-3), (4, 32, 64, 256, 2e-2)])
+def test_forward_matches_oracle(levels, base, H, W, tol):
+    net, params, x = setup_net(levels, base, H, W, seed=levels)
+    y = torch.zeros(3, H, W, device=DEV)
+    net.forward(torch.tensor(x, device=DEV), y)
+    ref, _ = ou.forward(params, x.astype(np.float64), levels, bf16_on=True)
+    got = y.cpu().numpy()
+    assert rel(got, ref) < tol, rel(got, ref)
+    ref64, _ = ou.forward(params, x.astype(np.float64), levels, bf16_on=False)
+    assert rel(got, ref64) < 5e-2
+
+
+@pytest.mark.parametrize("levels,base,H,W,layer_tol,flat_tol", [(2, 8, 8, 64, 2e-2, 2e-2),
+                                                                  (4, 16, 32, 256, 0.3, 0.15)])
+def test_parameter_gradient_matches_oracle(levels, base, H, W, layer_tol, flat_tol):
+    net, params, x = setup_net(levels, base, H, W, seed=10 + levels)
+    dy = np.random.default_rng(3).standard_normal((3, H, W)).astype(np.float32)
+    g = torch.zeros(net.num_params, device=DEV)
+    net.gradient(torch.tensor(x, device=DEV), torch.tensor(dy, device=DEV), g)
+    y, cache = ou.forward(params, x.astype(np.float64), levels, bf16_on=True)
+    grads, _ = ou.backward(cache, dy.astype(np.float64), levels, bf16_on=True)
+    got = learned.unpack(net.layers(), g.cpu().numpy())
+    for li, ((gw, gb_), (rw, rb)) in enumerate(zip(got, grads)):
+        assert rel(gw, rw) < layer_tol, (li, rel(gw, rw))
+        assert rel(gb_, rb) < layer_tol, (li, rel(gb_, rb))
+    fg = np.concatenate([np.concatenate([a.ravel(), b.ravel()]) for a, b in got])
+    fr = np.concatenate([np.concatenate([a.ravel(), b.ravel()]) for a, b in grads])
+    assert rel(fg, fr) < flat_tol
+    assert fg @ fr / (np.linalg.norm(fg) * np.linalg.norm(fr)) > 0.99
+    # padded entries of the flat gradient stay zero
+    repacked = learned.pack(net.layers(), got)
+    assert np.array_equal(repacked, g.cpu().numpy())
+
+
+def test_train_step_loss_and_first_adam_step():
+    levels, base, H, W = 3, 8, 16, 64
+    net, params, x = setup_net(levels, base, H, W, seed=21)
+    t = np.random.default_rng(4).standard_normal((3, H, W)).astype(np.float32)
+    xd, td = torch.tensor(x, device=DEV), torch.tensor(t, device=DEV)
+    y = torch.zeros(3, H, W, device=DEV)
+    net.forward(xd, y)
+    want_loss = float(np.mean((y.cpu().numpy().astype(np.float64) - t) ** 2))
+    dy = (2.0 * (y - td) / y.numel()).contiguous()
+    g = torch.zeros(net.num_params, device=DEV)
+    net.gradient(xd, dy, g)
+    p0 = torch.zeros(net.num_params, device=DEV)
+    net.get_params(p0)
+    lr = 1e-3
+    loss = net.train_step(xd[None].contiguous(), td[None].contiguous(), lr)
+    assert abs(loss - want_loss) <= 1e-5 * want_loss
+    p1 = torch.zeros(net.num_params, device=DEV)
+    net.get_params(p1)
+    # first Adam step: -lr g / (|g| + eps) (bias-corrected moments equal g, g^2)
+    step = (p1 - p0).cpu().numpy()
+    gv = g.cpu().numpy()
+    big = np.abs(gv) > 1e-4 * np.abs(gv).max()
+    assert np.allclose(step[big], -lr * np.sign(gv[big]), rtol=1e-3, atol=1e-7)
+
+
+def test_training_reduces_loss():
+    levels, base, H, W = 4, 16, 32, 128
+    net = gb.Unet(levels=levels, base=base, cin=5, cout=3, height=H, width=W)
+    net.set_params(torch.tensor(learned.he_init(net, 5), device=DEV))
+    rng = np.random.default_rng(6)
+    X = torch.tensor(rng.standard_normal((8, 5, H, W)).astype(np.float32), device=DEV)
+    # a smooth target that depends on the input: local averages of two channels
+    T = torch.nn.functional.avg_pool2d(X[:, :3], 5, stride=1, padding=2).contiguous()
+    losses = [net.train_step(X, T, 2e-3) for _ in range(60)]
+    assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
+
+
+def test_resample_matches_oracle():
+    rng = np.random.default_rng(7)
+    src = np.exp(rng.standard_normal((3, 17, 45))).astype(np.float32)
+    d = torch.zeros(3, 32, 128, device=DEV)
+    gb.resample(torch.tensor(src, device=DEV), d, op=1)
+    ref = ou.resample_bilinear(np.log(src.astype(np.float64)), 32, 128)
+    assert np.allclose(d.cpu().numpy(), ref, atol=1e-5)
+    back = torch.zeros(3, 17, 45, device=DEV)
+    gb.resample(d, back, op=2)
+    ref2 = np.exp(ou.resample_bilinear(ref, 17, 45))
+    assert rel(back.cpu().numpy(), ref2) < 1e-5
+
+
+@pytest.fixture(scope="module")
+def small_mesh():
+    wl = synth.marmousi_like_workload(nt=400, nshot=4, nex=64, nez=16, h=50.0)
+    srcs = [dict(s, f0=8.0, t0=0.15) for s in wl.sources(amp=1e12)]
+    m = gb.Mesh(wl.nex, wl.nez, wl.h, wl.dt, wl.nt, srcs, wl.rec_xz)
+    x, z = m.node_coords()
+    return wl, m, x, z
+
+
+def _model(x, z, seed, W, Hh):
+    return torch.tensor(np.stack(synth.marmousi_like(x, z, seed, W, Hh)), dtype=torch.float32, device=DEV)
+
+
+def test_features_match_oracle(small_mesh):
+    wl, m, x, z = small_mesh
+    mdl = _model(x, z, 3, wl.nex * wl.h, wl.nez * wl.h)
+    f = learned.features(m, mdl, 32, 128).cpu().numpy()
+    src_xz = [(s["x"], s["z"]) for s in wl.sources()]
+    rec = [(wl.rec_xz[i][0], wl.rec_xz[i][1]) for i in range(wl.nrec)] if np.ndim(wl.rec_xz) == 2 else \
+        [(wl.rec_xz[2 * i], wl.rec_xz[2 * i + 1]) for i in range(wl.nrec)]
+    node = ou.features(*[a.cpu().numpy() for a in mdl], x, z, src_xz, rec, learned.MASK_SIGMA_M)
+    ref = ou.resample_bilinear(node, 32, 128)
+    assert rel(f, ref) < 1e-5
+
+
+def test_precond_from_hessian_equals_precond_diag(small_mesh):
+    wl, m, x, z = small_mesh
+    mdl = _model(x, z, 4, wl.nex * wl.h, wl.nez * wl.h)
+    m.set_model(*[c.contiguous() for c in mdl])
+    H = torch.zeros_like(mdl)
+    B0 = torch.zeros_like(mdl)
+    m.precond_diag(list(range(wl.nshot)), 4, 100.0, 1.0, H, B0)
+    B0b = torch.zeros_like(mdl)
+    m.precond_from_hessian(H, 100.0, 1.0, B0b)
+    assert torch.equal(B0, B0b)
+
+
+def test_fallback_uses_computed_map_when_prediction_is_off(small_mesh):
+    wl, m, x, z = small_mesh
+    mdl = _model(x, z, 5, wl.nex * wl.h, wl.nez * wl.h)
+    net = gb.Unet(levels=4, base=8, cin=5, cout=3, height=32, width=128)
+    lp = learned.LearnedPreconditioner(net, seed=0)          # untrained: far off
+    H = learned.computed_map(m, mdl, list(range(wl.nshot)))
+    B0, info = lp.b0(m, mdl, 100.0, 1.0, computed_H=H)
+    assert info["fallback"] and info["rel_error"] > 0.2
+    ref = torch.zeros_like(mdl)
+    m.precond_from_hessian(H, 100.0, 1.0, ref)
+    assert torch.equal(B0, ref)
