@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--streams", type=int, default=4, help="single-shot launches simulated concurrently")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-unet", action="store_true", help="skip the learned-preconditioner timing")
     return ap.parse_args()
 
 
@@ -208,6 +209,61 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def time_unet(dev, peak_tflops: float, iters: int = 5, warmup: int = 3):
+    """The learned preconditioner at its full shape (4 levels, 32 base
+    channels, 5 -> 3 channels, 256 x 1024): inference and one training step
+    (batch 1) timed with CUDA events on the launching stream; tensor-core
+    fraction of the forward convolutions against the measured BF16 peak."""
+    import torch
+
+    import paper_2009_12663_gb300 as gb
+    from paper_2009_12663_gb300 import learned
+
+    H, W = 256, 1024
+    net = gb.Unet(levels=4, base=32, cin=5, cout=3, height=H, width=W)
+    net.set_params(torch.tensor(learned.he_init(net, 7), device=dev))
+    g = torch.Generator(device=dev).manual_seed(3)
+    x = torch.randn(5, H, W, device=dev, generator=g)
+    t = torch.randn(1, 3, H, W, device=dev, generator=g)
+    y = torch.zeros(3, H, W, device=dev)
+    # the convolutions of level l act on (H W) / 4^l pixels
+    flop = 0
+    lv = 4
+    shapes = net.layers()
+    li = 0
+    for l in range(lv):
+        for _ in range(2):
+            cout, cin, k = shapes[li][:3]
+            flop += 2 * cout * cin * k * k * (H * W >> (2 * l))
+            li += 1
+    for l in range(lv - 2, -1, -1):
+        for _ in range(2):
+            cout, cin, k = shapes[li][:3]
+            flop += 2 * cout * cin * k * k * (H * W >> (2 * l))
+            li += 1
+    cout, cin, k = shapes[li][:3]
+    flop += 2 * cout * cin * k * k * H * W
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for name, fn in (("inference", lambda: net.forward(x, y)),
+                     ("train_step", lambda: net.train_step(x[None].contiguous(), t, 1e-4))):
+        for _ in range(warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(iters):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name + "_ms"] = e0.elapsed_time(e1) / iters
+    tf = flop / (res["inference_ms"] / 1e3) / 1e12
+    return {"shape": "U-Net 4 levels x 32 base channels, 5 -> 3 channels, 256 x 1024, bf16 / fp32 accumulate",
+            "params": net.num_params, "conv_flop_per_inference": flop, **res,
+            "inference_tflops": tf, "bf16_peak_tflops": peak_tflops, "inference_frac_of_bf16_peak": tf / peak_tflops,
+            "note": "whole forward (im2col + GEMM + epilogues) over the convolution FLOPs; not part of `value`"}
+
 
 def run_ours(args):
     import torch
@@ -375,6 +431,10 @@ def run_ours(args):
             "forward_kernel": {"achieved": fwd_achieved, "frac": fwd_achieved / pk["hbm_gbs"],
                                "algorithmic_bytes_per_launch": fwd_unit, "avg_launch_us": fwd_us}}
 
+    unet = None
+    if not args.no_unet:
+        unet = time_unet(dev, pk.get("bf16_tflops", 1900.0))
+
     cpu = None
     if not args.no_cpu and world == 1:
         threads = max(1, min(os.cpu_count() or 1, 16))
@@ -397,6 +457,7 @@ def run_ours(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "learned_preconditioner": unet,
         "clocks": ck,
     }
     print(json.dumps(line), flush=True)

@@ -3,6 +3,7 @@ synthetic models (Section 3: BFGS vs L-BFGS(5), preconditioners P1-P4,
 RSVD uncertainty maps compared with the true model error).
 
     python -m paper_2009_12663_gb300.experiments [--iterations 15] [--out result.json]
+    python -m paper_2009_12663_gb300.experiments --learned [--out result.json]
 
 Prints one JSON document: per variant the relative data misfit and the
 relative model misfit (vp, vs) per iteration, iterations to halve the misfit,
@@ -29,6 +30,8 @@ import synth  # noqa: E402
 
 from . import Mesh  # noqa: E402
 from .fwi import Problem, fwi, model_misfit, preconditioner  # noqa: E402
+
+__all__ = ["build", "run", "learned_comparison"]
 
 
 def build(nex=80, nez=20, h=50.0, nshot=8, f0=8.0, nt=3000, seed=11, smooth=250.0, device="cuda"):
@@ -93,14 +96,110 @@ def run(iterations=15, sigma=100.0, rank=None):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--iterations", type=int, default=15)
+    ap.add_argument("--learned", action="store_true", help="run the learned-preconditioner comparison")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
-    res = run(a.iterations)
+    res = learned_comparison() if a.learned else run(a.iterations)
     txt = json.dumps(res)
     print(txt)
     if a.out:
         with open(a.out, "w") as f:
             f.write(json.dumps(res, indent=1))
+
+
+
+def learned_comparison(n_train=48, n_test=4, nt=3000, img=(256, 1024), steps=600, iterations=8, seed0=1000,
+                       device="cuda"):
+    """The learned preconditioner in kind of its intended use, on the
+    340 x 70 element Marmousi-shaped mesh (24 shots, 5 Hz, `nt` steps):
+    train the U-Net on P4 maps the method computes for seeded models, then
+    on a held-out model compare
+      plain:   one shot per launch, no graphs, P4 computed by the method;
+      fast:    four graph-replayed single-shot lanes, P4 predicted by the U-Net
+    by wall time to reach the misfit reduction the plain form reaches in
+    `iterations` BFGS iterations, and by the posterior std of the run."""
+    from . import Unet
+    from . import learned as L
+
+    wl = synth.marmousi_like_workload(nt=nt, nshot=24)
+    srcs = wl.sources(amp=1e12)
+    m = Mesh(wl.nex, wl.nez, wl.h, wl.dt, nt, srcs, wl.rec_xz)
+    x, z = m.node_coords()
+    W, H = wl.nex * wl.h, wl.nez * wl.h
+    ids = list(range(wl.nshot))
+    m.set_schedule(shots_per_launch=1, tile=0, use_graph=1, streams=4)
+
+    def model(s):
+        return torch.tensor(np.stack(synth.marmousi_like(x, z, s, W, H)), dtype=torch.float32, device=device)
+
+    t0 = time.perf_counter()
+    models = [model(seed0 + i) for i in range(n_train + n_test)]
+    X, T = L.make_pairs(m, models, ids, *img)
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    net = Unet(levels=4, base=32, cin=5, cout=3, height=img[0], width=img[1])
+    lp = L.LearnedPreconditioner(net, seed=1)
+    t_train = lp.fit(X[:n_train], T[:n_train], steps=steps, lr=1e-3, batch=4, seed=2, lr_decay=0.997)
+    errs = []
+    for i in range(n_train, n_train + n_test):
+        Hc = L.computed_map(m, models[i], ids)
+        errs.append(L.rel_log_error(lp.predict_map(m, models[i]), Hc))
+    out = {"workload": f"340x70 Marmousi-shaped mesh, 24 shots x {nt} steps; U-Net 4 x 32 on {img[0]}x{img[1]}",
+           "train_pairs": n_train, "test_models": n_test, "pair_generation_s": t_pairs, "train_steps": steps,
+           "train_s": t_train, "loss_first_last": [lp.history[0], lp.history[-1]],
+           "heldout_rel_log_error": errs}
+
+    # inversion of a held-out truth from its smoothed start
+    truth = models[n_train]
+    start = torch.tensor(np.stack(synth.marmousi_like_smooth(x, z, seed0 + n_train, W, H)),
+                         dtype=torch.float32, device=device)
+    d_obs = torch.zeros(wl.nshot, wl.nrec, 2, nt, device=device)
+    m.set_model(*truth)
+    m.forward(ids, d_obs)
+    prob = Problem(m, ids, d_obs, invert=(False, True, True))
+
+    def run(schedule, b0_fn, target=None):
+        m.set_schedule(**schedule)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B0, info = b0_fn()
+        torch.cuda.synchronize()
+        t_b0 = time.perf_counter() - t0
+        trace = []
+        cb = lambda it, mk, h: trace.append((h["rel_misfit"], time.perf_counter() - t0))
+        mi, hist, store = fwi(prob, start, iterations, B0=B0, callback=cb)
+        reach = None
+        if target is not None:
+            reach = next((t for r, t in trace if r <= target), None)
+        k = store.count
+        std = torch.zeros(store.n, device=device)
+        store.lowrank_invhess(k, k, seed=2020, eps_prior=1.0, std=std)
+        return {"b0_s": t_b0, "b0_info": info, "rel_misfit": [h["rel_misfit"] for h in hist],
+                "trace_s": [t for _, t in trace], "time_to_target_s": reach}, std
+
+    plain_sched = dict(shots_per_launch=1, tile=0, use_graph=0, ckpt_every=0, streams=1)
+    fast_sched = dict(shots_per_launch=1, tile=0, use_graph=1, ckpt_every=0, streams=4)
+
+    def computed():
+        return preconditioner(m, ids, start, 4, 100.0), {"source": "computed P4"}
+
+    def predicted():
+        B0, info = lp.b0(m, start, 100.0, 1.0)
+        info["source"] = "U-Net"
+        return B0, info
+
+    plain, std_p = run(plain_sched, computed)
+    target = plain["rel_misfit"][-1]
+    plain["time_to_target_s"] = plain["trace_s"][-1]
+    fast, std_f = run(fast_sched, predicted, target)
+    fast_computed, std_fc = run(fast_sched, computed, target)
+    out["target_rel_misfit"] = target
+    out["plain_single_shot_computed_P4"] = plain
+    out["fast_lanes_graphs_learned_P4"] = fast
+    out["fast_lanes_graphs_computed_P4"] = fast_computed
+    out["posterior_std_rel_diff_learned_vs_computed"] = float((std_f - std_p).norm() / std_p.norm())
+    out["posterior_std_rel_diff_fast_vs_plain_computed"] = float((std_fc - std_p).norm() / std_p.norm())
+    return out
 
 
 if __name__ == "__main__":
