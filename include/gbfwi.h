@@ -211,11 +211,12 @@ int gbfwi_bfgs_apply(gbfwi_bfgs *b, const float *X, int p, float *Z, double gamm
  * X: [p][n] probing block, or NULL to draw standard normals on the device
  * from Philox4x32-10 with `seed` (counter = element index / 4).  V: [rank][n]
  * (may be NULL), lambda: [rank] FP64 (may be NULL), std: [n] (may be NULL).
- * Q spans the directions of E whose singular value is at least 1e-4 of the
- * largest (the FP64 Gram E E^T is eigendecomposed; an FP32 block resolves
- * nothing finer), so r = dim Q <= p; Omega (r x r) is then the least-squares
- * solution, equal to the solve above when r = p, and eigenpairs beyond r are
- * returned as lambda = 0 with zero rows of V.
+ * Q is rank-revealing: pivoted Cholesky of the FP64 Gram matrix E E^T (QR
+ * with column pivoting on E) keeps the probe rows whose residual norm is at
+ * least 1e-4 of the largest (an FP32 block resolves nothing finer), so
+ * r = dim Q <= p; Omega (r x r) is then the least-squares solution, equal to
+ * the solve above when r = p, and eigenpairs beyond r are returned as
+ * lambda = 0 with zero rows of V.
  * 1 <= rank <= p <= 256.  Synchronises the stream.
  * -> EINVAL, ECUDA, ENOMEM, ENONFINITE (E = 0 or non-finite, a singular
  *    Q^T X). */

@@ -141,6 +141,46 @@ __global__ void __launch_bounds__(256) atb_partial(const float *__restrict__ A, 
         }
 }
 
+// Thin form of atb_partial for kb <= 2 columns (dot products of the pair
+// updates, the search direction): CTA (split, a) accumulates row a against
+// the kb columns with compensated (Dot2) sums, then an FP64 tree over its
+// threads; same partial layout as atb_partial.
+template <int KB>
+__global__ void __launch_bounds__(256) atb_thin(const float *__restrict__ A, long long lda,
+                                                const float *__restrict__ Bm, long long ldb,
+                                                const float *__restrict__ w, long long n, long long chunk, int ka,
+                                                double *__restrict__ part)
+{
+    __shared__ double red[KB][256];
+    const int sx = blockIdx.x, a = blockIdx.y, t = threadIdx.x;
+    const long long ib = (long long)sx * chunk, ie = min(n, ib + chunk);
+    float hi[KB], lo[KB];
+#pragma unroll
+    for (int b = 0; b < KB; ++b) hi[b] = lo[b] = 0.f;
+    const float *ar = A + (long long)a * lda;
+    for (long long i = ib + t; i < ie; i += blockDim.x) {
+        const float av = __ldg(ar + i);
+#pragma unroll
+        for (int b = 0; b < KB; ++b) {
+            float bv = __ldg(Bm + (long long)b * ldb + i);
+            if (w) bv *= __ldg(w + i);
+            dot2_term(av, bv, hi[b], lo[b]);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < KB; ++b) red[b][t] = (double)hi[b] + (double)lo[b];
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (t < h)
+#pragma unroll
+            for (int b = 0; b < KB; ++b) red[b][t] += red[b][t + h];
+        __syncthreads();
+    }
+    if (t == 0)
+#pragma unroll
+        for (int b = 0; b < KB; ++b) part[((long long)sx * ka + a) * KB + b] = red[b][0];
+}
+
 __global__ void atb_reduce(const double *__restrict__ part, int nsplit, int nab, double *__restrict__ out,
                            long long ldo, int kb)
 {
@@ -322,26 +362,30 @@ __global__ void chol_kernel(const double *__restrict__ G, int p, double shift, d
 // p/2 disjoint rotations per round.  A pair is rotated only while
 // |a_pq| > 1e-15 sqrt(|a_pp a_qq|) (the relative threshold of Demmel &
 // Veselic 1992, which also resolves small eigenvalues of a graded matrix)
-// and |a_pq| > 1e-16 |A|_F (below that an entry is FP64 rounding noise of
-// the largest eigenvalues); the sweeps stop after one without a rotation,
-// or after max_sweeps.  cs: scratch of >= p + 1 doubles.
-__device__ void block_jacobi(double *A, double *U, int p, double *cs, int max_sweeps)
+// and |a_pq| > eps |A|_F (below that an entry is rounding noise of the
+// largest eigenvalues), with eps 1e-15 / 1e-16 in FP64 and 1e-7 / 1e-7 in
+// FP32; the sweeps stop after one without a rotation, or after max_sweeps.
+// cs: scratch of >= p + 1 elements.
+template <typename T>
+__device__ void block_jacobi(T *A, T *U, int p, T *cs, int max_sweeps)
 {
     const int t = threadIdx.x, nt = blockDim.x;
+    constexpr T rel_eps = sizeof(T) == 8 ? (T)1e-15 : (T)1e-7;
+    constexpr T abs_eps = sizeof(T) == 8 ? (T)1e-16 : (T)1e-7;
     __shared__ int rotated;
-    __shared__ double fro;
+    __shared__ T fro;
     const int P = (p + 1) & ~1;
     const int npair = P / 2;
     __syncthreads();
-    if (t == 0) fro = 0.0;
+    if (t == 0) fro = 0;
     __syncthreads();
     {
-        double f = 0.0;
+        T f = 0;
         for (int q = t; q < p * p; q += nt) f += A[q] * A[q];
         atomicAdd(&fro, f);
     }
     __syncthreads();
-    const double abs_tol = 1e-16 * sqrt(fro);
+    const T abs_tol = abs_eps * sqrt(fro);
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         __syncthreads();
         if (t == 0) rotated = 0;
@@ -350,15 +394,15 @@ __device__ void block_jacobi(double *A, double *U, int p, double *cs, int max_sw
             for (int m = t; m < npair; m += nt) {
                 int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
                 int b = 1 + (P - 2 - m + round) % (P - 1);
-                double c = 1.0, sn = 0.0;
+                T c = 1, sn = 0;
                 if (a < p && b < p) {
                     int pp = min(a, b), qq = max(a, b);
-                    double apq = A[(long long)pp * p + qq];
-                    double app = A[(long long)pp * p + pp], aqq = A[(long long)qq * p + qq];
-                    if (fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && fabs(apq) > abs_tol) {
-                        double tau = (aqq - app) / (2.0 * apq);
-                        double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + tt * tt);
+                    T apq = A[(long long)pp * p + qq];
+                    T app = A[(long long)pp * p + pp], aqq = A[(long long)qq * p + qq];
+                    if (fabs(apq) > rel_eps * sqrt(fabs(app * aqq)) && fabs(apq) > abs_tol) {
+                        T tau = (aqq - app) / (2 * apq);
+                        T tt = (tau >= 0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
+                        c = (T)1 / sqrt((T)1 + tt * tt);
                         sn = tt * c;
                         rotated = 1;
                     }
@@ -371,10 +415,10 @@ __device__ void block_jacobi(double *A, double *U, int p, double *cs, int max_sw
                 int m = q / p, l = q % p;
                 int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
                 int b = 1 + (P - 2 - m + round) % (P - 1);
-                if (a >= p || b >= p || cs[2 * m + 1] == 0.0) continue;
+                if (a >= p || b >= p || cs[2 * m + 1] == 0) continue;
                 int pp = min(a, b), qq = max(a, b);
-                double c = cs[2 * m], sn = cs[2 * m + 1];
-                double x = A[(long long)pp * p + l], y = A[(long long)qq * p + l];
+                T c = cs[2 * m], sn = cs[2 * m + 1];
+                T x = A[(long long)pp * p + l], y = A[(long long)qq * p + l];
                 A[(long long)pp * p + l] = c * x - sn * y;
                 A[(long long)qq * p + l] = sn * x + c * y;
             }
@@ -383,13 +427,13 @@ __device__ void block_jacobi(double *A, double *U, int p, double *cs, int max_sw
                 int m = q / p, l = q % p;
                 int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
                 int b = 1 + (P - 2 - m + round) % (P - 1);
-                if (a >= p || b >= p || cs[2 * m + 1] == 0.0) continue;
+                if (a >= p || b >= p || cs[2 * m + 1] == 0) continue;
                 int pp = min(a, b), qq = max(a, b);
-                double c = cs[2 * m], sn = cs[2 * m + 1];
-                double x = A[(long long)l * p + pp], y = A[(long long)l * p + qq];
+                T c = cs[2 * m], sn = cs[2 * m + 1];
+                T x = A[(long long)l * p + pp], y = A[(long long)l * p + qq];
                 A[(long long)l * p + pp] = c * x - sn * y;
                 A[(long long)l * p + qq] = sn * x + c * y;
-                double u = U[(long long)l * p + pp], v = U[(long long)l * p + qq];
+                T u = U[(long long)l * p + pp], v = U[(long long)l * p + qq];
                 U[(long long)l * p + pp] = c * u - sn * v;
                 U[(long long)l * p + qq] = sn * u + c * v;
             }
@@ -400,44 +444,88 @@ __device__ void block_jacobi(double *A, double *U, int p, double *cs, int max_sw
     __syncthreads();
 }
 
-// Rank-revealing orthonormalisation of the probe block E [p][n] from its
-// FP64 Gram G = E E^T = W S^2 W^T: keep the r directions with singular value
-// >= tol * s_max and return coef [r][p] with Q1 = coef E = S_r^-1 W_r^T E;
-// *r_out = r.  An FP32 block carries ~1e-7 relative rounding, so directions
-// far below s_max are noise: combining them would amplify that rounding by
-// s_max / s_i, which is where plain CholeskyQR on E breaks down.
-__global__ void gram_basis_kernel(const double *__restrict__ G, int p, double tol, double *work,
-                                  float *__restrict__ coef, int *__restrict__ r_out, int *__restrict__ flag,
-                                  int use_smem)
+// Rank-revealing basis of the probe block E [p][n] from its FP64 Gram matrix
+// G = E E^T by diagonally pivoted Cholesky (the normal-equations form of QR
+// with column pivoting on E): at step j the row of E with the largest
+// remaining residual norm is taken, and the factorisation stops once that
+// norm falls below tol times the largest row norm.  With the r selected rows
+// E_s (permutation piv) and G_ss = R^T R, Q1 = R^-T E_s has orthonormal rows
+// spanning them; the returned coef [r][p] gives Q1 = coef E (zero columns for
+// the rows not taken).  An FP32 block carries ~1e-7 relative rounding, so
+// directions far below the largest are noise: taking them would amplify
+// that rounding by s_max / s_i.  work: >= 3 p^2 doubles + p ints.
+__global__ void gram_pivchol_kernel(const double *__restrict__ G, int p, double tol, double *work,
+                                    float *__restrict__ coef, int *__restrict__ r_out, int *__restrict__ flag,
+                                    int use_smem)
 {
     extern __shared__ double smem_work[];
     if (use_smem) work = smem_work;
     const int t = threadIdx.x, nt = blockDim.x;
-    double *A = work, *U = A + (long long)p * p, *cs = U + (long long)p * p;
-    for (int q = t; q < p * p; q += nt) {
+    const long long pp = (long long)p * p;
+    double *A = work, *R = A + pp, *Ri = R + pp;
+    int *piv = reinterpret_cast<int *>(Ri + pp);
+    __shared__ int s_r, s_go;
+    __shared__ double s_d, s_d0;
+    for (long long q = t; q < pp; q += nt) {
         A[q] = G[q];
-        U[q] = (q / p == q % p) ? 1.0 : 0.0;
+        R[q] = 0.0;
     }
-    block_jacobi(A, U, p, cs, 60);
-    if (t == 0) {
-        int *used = reinterpret_cast<int *>(cs);
-        double smax = 0.0;
-        for (int i = 0; i < p; ++i) { used[i] = 0; smax = fmax(smax, A[(long long)i * p + i]); }
-        if (!(smax > 0.0) || !isfinite(smax)) *flag = 1;
-        int r = 0;
-        for (int c = 0; c < p; ++c) {
+    for (int i = t; i < p; i += nt) piv[i] = i;
+    if (t == 0) s_r = p;
+    __syncthreads();
+    for (int j = 0; j < p; ++j) {
+        if (t == 0) {
             int best = -1;
             double bv = -1.0;
-            for (int i = 0; i < p; ++i)
-                if (!used[i] && A[(long long)i * p + i] > bv) { bv = A[(long long)i * p + i]; best = i; }
-            if (best < 0 || !(bv > 0.0) || sqrt(bv) < tol * sqrt(smax)) break;
-            used[best] = 1;
-            const double inv = 1.0 / sqrt(bv);
-            for (int a = 0; a < p; ++a) coef[(long long)r * p + a] = (float)(U[(long long)a * p + best] * inv);
-            ++r;
+            for (int k = j; k < p; ++k) {
+                double d = A[(long long)piv[k] * p + piv[k]];
+                if (d > bv) { bv = d; best = k; }
+            }
+            if (j == 0) {
+                s_d0 = bv;
+                if (!(bv > 0.0) || !isfinite(bv)) *flag = 1;
+            }
+            if (best < 0 || !(bv > tol * tol * s_d0)) {
+                s_r = j;
+                s_go = 0;
+            } else {
+                int tmp = piv[j];
+                piv[j] = piv[best];
+                piv[best] = tmp;
+                s_d = sqrt(bv);
+                R[(long long)j * p + j] = s_d;
+                s_go = 1;
+            }
         }
-        *r_out = r;
+        __syncthreads();
+        if (!s_go) break;
+        const int pj = piv[j];
+        const double d = s_d;
+        for (int k = j + 1 + t; k < p; k += nt) R[(long long)j * p + k] = A[(long long)pj * p + piv[k]] / d;
+        __syncthreads();
+        const int m = p - j - 1;
+        for (int q = t; q < m * m; q += nt) {
+            const int kk = j + 1 + q / m, ll = j + 1 + q % m;
+            A[(long long)piv[kk] * p + piv[ll]] -= R[(long long)j * p + kk] * R[(long long)j * p + ll];
+        }
+        __syncthreads();
     }
+    const int r = s_r;
+    // R11^-1 (upper, r x r) by back substitution, one column per thread
+    for (int c = t; c < r; c += nt)
+        for (int i = r - 1; i >= 0; --i) {
+            double sacc = (i == c) ? 1.0 : 0.0;
+            for (int k = i + 1; k <= c; ++k) sacc -= R[(long long)i * p + k] * Ri[(long long)k * r + c];
+            Ri[(long long)i * r + c] = sacc / R[(long long)i * p + i];
+        }
+    for (long long q = t; q < (long long)r * p; q += nt) coef[q] = 0.f;
+    __syncthreads();
+    // coef[a][piv[b]] = (R11^-T)[a][b] = R11^-1[b][a]
+    for (int q = t; q < r * r; q += nt) {
+        const int a = q / r, b = q % r;
+        coef[(long long)a * p + piv[b]] = (float)Ri[(long long)b * r + a];
+    }
+    if (t == 0) *r_out = r;
 }
 
 // Single-pass randomized SVD core (Algorithm 3) with r <= p basis vectors:
@@ -505,14 +593,19 @@ __global__ void omega_ls_kernel(const double *__restrict__ QE, const double *__r
             if (rr != j) Aug[(long long)rr * 2 * r + j] = 0.0;
         __syncthreads();
     }
+    // Omega symmetrised, eigendecomposed in FP32 (absolute eigenvalue error
+    // ~1e-7 |Omega|; FP64 sweeps cost ~60x more on this part)
+    float *Af = reinterpret_cast<float *>(U);             // r^2 floats
+    float *Uf = Af + (long long)r * r;                     // r^2 floats (U holds 2 r^2)
+    float *csf = reinterpret_cast<float *>(cs);
     for (int q = t; q < r * r; q += nt) {
         int i = q / r, j = q % r;
         double oij = Aug[(long long)j * 2 * r + r + i];   // Omega[i][j] = Omega^T[j][i]
         double oji = Aug[(long long)i * 2 * r + r + j];
-        A[q] = 0.5 * (oij + oji);
-        U[q] = (i == j) ? 1.0 : 0.0;
+        Af[q] = (float)(0.5 * (oij + oji));
+        Uf[q] = (i == j) ? 1.f : 0.f;
     }
-    block_jacobi(A, U, r, cs, 60);
+    block_jacobi<float>(Af, Uf, r, csf, 60);
     if (t == 0) {
         int *used = reinterpret_cast<int *>(cs);
         for (int i = 0; i < r; ++i) used[i] = 0;
@@ -523,10 +616,10 @@ __global__ void omega_ls_kernel(const double *__restrict__ QE, const double *__r
                 continue;
             }
             int best = -1;
-            double bv = -1.0;
+            float bv = -1.f;
             for (int i = 0; i < r; ++i) {
                 if (used[i]) continue;
-                double v = fabs(A[(long long)i * r + i]);
+                float v = fabsf(Af[(long long)i * r + i]);
                 if (v > bv) { bv = v; best = i; }
             }
             if (best < 0) {                     // non-finite diagonal
@@ -534,8 +627,8 @@ __global__ void omega_ls_kernel(const double *__restrict__ QE, const double *__r
                 for (best = 0; used[best]; ++best) {}
             }
             used[best] = 1;
-            lam[k] = A[(long long)best * r + best];
-            for (int a2 = 0; a2 < r; ++a2) coef[(long long)k * r + a2] = (float)U[(long long)a2 * r + best];
+            lam[k] = (double)Af[(long long)best * r + best];
+            for (int a2 = 0; a2 < r; ++a2) coef[(long long)k * r + a2] = Uf[(long long)a2 * r + best];
         }
     }
 }
@@ -604,6 +697,19 @@ int atb(gbfwi_bfgs *h, const float *A, long long lda, int ka, const float *Bm, l
     long long chunk = ((n + nsplit - 1) / nsplit + KI - 1) / KI * KI;
     nsplit = (n + chunk - 1) / chunk;
     GB_TRY(h->part.ensure((size_t)nsplit * ka * kb * sizeof(double)));
+    if (kb <= 2) {
+        // one or two columns: a thin, always compensated pass
+        dim3 tg((unsigned)nsplit, (unsigned)ka);
+        if (kb == 1)
+            atb_thin<1><<<tg, 256, 0, s>>>(A, lda, Bm, ldb, w, n, chunk, ka, h->part.as<double>());
+        else
+            atb_thin<2><<<tg, 256, 0, s>>>(A, lda, Bm, ldb, w, n, chunk, ka, h->part.as<double>());
+        GB_LAUNCHED();
+        int nab = ka * kb;
+        atb_reduce<<<(nab + 255) / 256, 256, 0, s>>>(h->part.as<double>(), (int)nsplit, nab, out, ldo, kb);
+        GB_LAUNCHED();
+        return GBFWI_OK;
+    }
     dim3 grid((unsigned)nsplit, (ka + AT - 1) / AT, (kb + AT - 1) / AT);
     if (accurate)
         atb_partial<true><<<grid, 256, 0, s>>>(A, lda, ka, Bm, ldb, kb, w, n, chunk, h->part.as<double>());
@@ -829,10 +935,12 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
     GB_TRY(reserve(h, p, true));
     float *E = h->E.as<float>(), *Q = h->Q.as<float>();
     // 1. E = (B_{n+1} - B0) X
-    GB_TRY(apply_dev(h, Xd, p, E, 1.0, 1, s));
-    // 2. rank-revealing basis of E: FP64 Gram eigendecomposition, directions
-    //    with relative singular value >= 1e-4 (resolved by an FP32 block),
-    //    then one CholeskyQR pass to restore orthonormality in FP32
+    // (coefficients S^T X, (B0 Y)^T X with compensated sums: E feeds the eigenvectors)
+    GB_TRY(apply_dev(h, Xd, p, E, 1.0, 1, s, true));
+    // 2. rank-revealing basis of E: pivoted Cholesky of its FP64 Gram matrix,
+    //    rows kept while their residual norm is >= 1e-4 of the largest (what an
+    //    FP32 block resolves), then one CholeskyQR pass to restore
+    //    orthonormality in FP32
     const size_t pp = (size_t)p * p;
     double *G = h->small.as<double>() + small_apply_doubles(h, p);
     double *A = G + pp, *R2 = A + pp, *Rinv = R2 + pp, *QE = Rinv + pp, *QX = QE + pp;
@@ -845,26 +953,34 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
     const size_t ws = (4 * pp + 4 * (size_t)p) * sizeof(double);
     const int use_smem = ws <= 200 * 1024;
     if (use_smem) {
-        GB_CUDA(cudaFuncSetAttribute(gram_basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
+        GB_CUDA(cudaFuncSetAttribute(gram_pivchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
         GB_CUDA(cudaFuncSetAttribute(omega_ls_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
     }
     GB_TRY(atb(h, E, n, p, E, n, p, nullptr, G, p, s, true));
-    gram_basis_kernel<<<1, 512, use_smem ? ws : 0, s>>>(G, p, 1e-4, work, coef, rdev, flag, use_smem);
+    gram_pivchol_kernel<<<1, 512, use_smem ? ws : 0, s>>>(G, p, 1e-4, work, coef, rdev, flag, use_smem);
     GB_LAUNCHED();
     int r = 0;
     GB_CUDA(cudaMemcpyAsync(&r, rdev, sizeof(int), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     if (r < 1) return gb_nonfinite("probe block E = (B - B0) X is zero or not finite");
     GB_TRY(combine(h, E, nullptr, p, p, coef, r, Q, nullptr, nullptr, 0.f, s));   // Q1 [r][n] in Q
-    GB_TRY(atb(h, Q, n, r, Q, n, r, nullptr, G, r, s, true));
+    GB_TRY(atb(h, Q, n, r, Q, n, r, nullptr, G, r, s));          // Q1 nearly orthonormal: FP32 sums
     chol_kernel<<<1, 256, 0, s>>>(G, r, 0.0, A, R2, Rinv, coef, flag);
     GB_LAUNCHED();
     float *Qf = h->V.as<float>();
     GB_TRY(h->V.ensure((size_t)p * n * sizeof(float)));
     Qf = h->V.as<float>();
     GB_TRY(combine(h, Q, nullptr, r, r, coef, r, Qf, nullptr, nullptr, 0.f, s));  // Q [r][n]
+    // second CholeskyQR pass (CholeskyQR2): the rounding of the first leaves
+    // Q orthonormal only to ~eps cond(R11), which Algorithm 3 amplifies
+    GB_TRY(atb(h, Qf, n, r, Qf, n, r, nullptr, G, r, s));
+    chol_kernel<<<1, 256, 0, s>>>(G, r, 0.0, A, R2, Rinv, coef, flag);
+    GB_LAUNCHED();
+    GB_TRY(combine(h, Qf, nullptr, r, r, coef, r, Q, nullptr, nullptr, 0.f, s));
+    std::swap(Q, Qf);                     // Qf: the basis; Q: free
     // 3. Q^T E, Q^T X ; Omega by least squares ; eigenpairs
     GB_TRY(atb(h, Qf, n, r, E, n, p, nullptr, QE, p, s, true));
+    // Q^T X compensated too: Omega = (Q^T E)(Q^T X)^-1 amplifies its error by cond(Q^T X)
     GB_TRY(atb(h, Qf, n, r, Xd, n, p, nullptr, QX, p, s, true));
     omega_ls_kernel<<<1, 512, use_smem ? ws : 0, s>>>(QE, QX, r, p, rank, work, lam, coef, flag, use_smem);
     GB_LAUNCHED();

@@ -79,9 +79,10 @@ def preconditioner(mesh: Mesh, shot_ids, m0: torch.Tensor, kind: int, sigma: flo
 
 
 def fwi(problem: Problem, m0: torch.Tensor, iterations: int, B0=None, memory=None, step0=0.02,
-        c1=1e-4, max_backtracks=8, callback=None):
+        c1=1e-4, max_backtracks=8, callback=None, pairs_out=None):
     """Run (L-)BFGS.  Returns (model, history, store); `store` is the
-    full-history BFGS store (None for L-BFGS) that lowrank_invhess probes."""
+    full-history BFGS store (None for L-BFGS) that lowrank_invhess probes.
+    When `pairs_out` is a list, every stored pair (s, y) is appended to it."""
     mask = problem.mask
     m = clamp_model(m0.clone())
     n = int(mask.sum()) * m[0].numel()
@@ -138,6 +139,8 @@ def fwi(problem: Problem, m0: torch.Tensor, iterations: int, B0=None, memory=Non
             if store is not None:
                 store.update(s_vec, y_vec)
             pairs.append((s_vec, y_vec))
+            if pairs_out is not None:
+                pairs_out.append((s_vec.clone(), y_vec.clone()))
         except GbfwiError as e:
             if e.name != "ECURV":
                 raise

@@ -1,14 +1,14 @@
 """Learned diagonal preconditioner around the C ABI: a U-Net (gbfwi_unet)
 trained on the pseudo-Hessian maps the method itself computes (P4 of
 Eqs. 7-8 / A22, gbfwi_precond_diag), used to predict B0 for a new model,
-with the computed map as fallback and as the judge of its error.
+with the computed map as fallback and as the measure of its error.
 
 Argument marshalling and bookkeeping only: features, resampling, the
 network's forward / backward / Adam steps and the smoothing-damping-
 inversion into B0 all run in the CUDA library.
 
-    pairs = make_pairs(mesh, models, shot_ids)          # (features, log-H targets)
-    lp = LearnedPreconditioner(Unet(...)); lp.fit(pairs, steps=...)
+    X, T = make_pairs(mesh, models, shot_ids, 256, 1024)   # features, log-H targets
+    lp = LearnedPreconditioner(Unet(...)); lp.fit(X, T, steps=...)
     B0, info = lp.b0(mesh, model, sigma, damp, computed_H=None)
 """
 from __future__ import annotations

@@ -77,7 +77,7 @@ def test_autograd_gradient_against_finite_differences(setup):
         ans.append(float(sum((gc * d).sum() for gc, d in zip(g, dm))))
     fds, ans = np.array(fds), np.array(ans)
     rel_err = np.abs(fds - ans) / np.abs(ans)
-    # directions whose derivative nearly cancels are judged against the
+    # directions whose derivative nearly cancels are compared with the
     # typical derivative size instead of their own
     scaled = np.abs(fds - ans) / np.sqrt(np.mean(ans ** 2))
     print("FD: median relative error %.2e, max error / rms derivative %.2e" % (np.median(rel_err), scaled.max()))
