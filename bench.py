@@ -431,6 +431,19 @@ def run_ours(args):
             "forward_kernel": {"achieved": fwd_achieved, "frac": fwd_achieved / pk["hbm_gbs"],
                                "algorithmic_bytes_per_launch": fwd_unit, "avg_launch_us": fwd_us}}
 
+    # exact low-rank decomposition of the same 50-pair store (no probes),
+    # timed after the timed region
+    for _ in range(2):
+        uq.lowrank_exact(rnk, eps_prior=1.0, V=V, lam=lam, std=std)
+    ex0, ex1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ex0.record(stream)
+    for _ in range(3):
+        uq.lowrank_exact(rnk, eps_prior=1.0, V=V, lam=lam, std=std)
+    ex1.record(stream)
+    torch.cuda.synchronize()
+    uq_exact = {"s_per_call": ex0.elapsed_time(ex1) / 3e3, "pairs": 50, "rank": rnk,
+                "note": "gbfwi_lowrank_exact: QR of [S, B0 Y] instead of probes; not part of `value`"}
+
     unet = None
     if not args.no_unet:
         unet = time_unet(dev, pk.get("bf16_tflops", 1900.0))
@@ -457,6 +470,7 @@ def run_ours(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "uq_exact": uq_exact,
         "learned_preconditioner": unet,
         "clocks": ck,
     }

@@ -188,6 +188,11 @@ class Bfgs:
                                           float(eps_prior), ptr(V, F32), ptr(lam, F64), ptr(std, F32),
                                           stream_of(X, V, lam, std)), "lowrank_invhess")
 
+    def lowrank_exact(self, rank, eps_prior=1.0, V=None, lam=None, std=None):
+        """Exact eigenpairs of B_{n+1} - B0 (rank <= 2k) from a QR of [S, B0 Y]."""
+        check(lib().gbfwi_lowrank_exact(self._h, int(rank), float(eps_prior), ptr(V, F32), ptr(lam, F64),
+                                        ptr(std, F32), stream_of(V, lam, std)), "lowrank_exact")
+
 
 # function-style names of the C ABI
 def mesh_create(*a, **k) -> Mesh:

@@ -35,6 +35,7 @@ struct gbfwi_bfgs {
     DevBuf X, E, Q, V;         // [p][n] blocks
     DevBuf stage;              // host staging
     DevBuf flag;
+    DevBuf ex;                 // FP64 scratch of the exact low-rank decomposition
 };
 
 namespace {
@@ -633,6 +634,96 @@ __global__ void omega_ls_kernel(const double *__restrict__ QE, const double *__r
     }
 }
 
+// d_i = 1 / sqrt(G_ii) (0 for an empty row), G <- D G D: the pivoted
+// Cholesky then compares directions, not the scales of S and B0 Y
+__global__ void gram_scale_kernel(double *__restrict__ G, int m, double *__restrict__ d)
+{
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double g = G[(long long)i * m + i];
+        d[i] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < m * m; q += blockDim.x) G[q] *= d[q / m] * d[q % m];
+}
+
+// coef [r][m] <- coef D (undo the column scaling in the combination)
+__global__ void coef_colscale_kernel(float *__restrict__ coef, int r, int m, const double *__restrict__ d)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < r * m; q += gridDim.x * blockDim.x)
+        coef[q] = (float)((double)coef[q] * d[q % m]);
+}
+
+// T = C M C^T (symmetrised), C [r][m], M [m][m] symmetric, FP64, one CTA;
+// P [r][m] scratch
+__global__ void exact_t_kernel(const double *__restrict__ C, const double *__restrict__ M, int r, int m,
+                               double *__restrict__ P, double *__restrict__ T)
+{
+    for (int q = threadIdx.x; q < r * m; q += blockDim.x) {
+        const int a = q / m, c = q % m;
+        double acc = 0.0;
+        for (int b = 0; b < m; ++b) acc += C[(long long)a * m + b] * M[(long long)b * m + c];
+        P[q] = acc;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < r * r; q += blockDim.x) {
+        const int a = q / r, b = q % r;
+        if (b < a) continue;
+        double ab = 0.0, ba = 0.0;
+        for (int c = 0; c < m; ++c) {
+            ab += P[(long long)a * m + c] * C[(long long)b * m + c];
+            ba += P[(long long)b * m + c] * C[(long long)a * m + c];
+        }
+        const double v = 0.5 * (ab + ba);
+        T[(long long)a * r + b] = v;
+        T[(long long)b * r + a] = v;
+    }
+}
+
+// Eigenpairs of a symmetric r x r matrix T (FP32 block Jacobi), ordered by
+// |lambda| descending: lam[rank] and coef [rank][r] = U^T (zero rows
+// beyond r).  work: >= r^2 + r + 8 doubles (or shared memory).
+__global__ void eig_select_kernel(const double *__restrict__ T, int r, int rank, double *work,
+                                  double *__restrict__ lam, float *__restrict__ coef, int *__restrict__ flag,
+                                  int use_smem)
+{
+    extern __shared__ double smem_work[];
+    if (use_smem) work = smem_work;
+    const int t = threadIdx.x, nt = blockDim.x;
+    float *Af = reinterpret_cast<float *>(work);
+    float *Uf = Af + (long long)r * r;
+    float *csf = Uf + (long long)r * r;            // >= r + 2 floats
+    for (int q = t; q < r * r; q += nt) {
+        Af[q] = (float)T[q];
+        Uf[q] = (q / r == q % r) ? 1.f : 0.f;
+    }
+    block_jacobi<float>(Af, Uf, r, csf, 60);
+    if (t == 0) {
+        int *used = reinterpret_cast<int *>(csf);
+        for (int i = 0; i < r; ++i) used[i] = 0;
+        for (int k = 0; k < rank; ++k) {
+            if (k >= r) {
+                lam[k] = 0.0;
+                for (int a = 0; a < r; ++a) coef[(long long)k * r + a] = 0.f;
+                continue;
+            }
+            int best = -1;
+            float bv = -1.f;
+            for (int i = 0; i < r; ++i) {
+                if (used[i]) continue;
+                float v = fabsf(Af[(long long)i * r + i]);
+                if (v > bv) { bv = v; best = i; }
+            }
+            if (best < 0) {
+                *flag = 4;
+                for (best = 0; used[best]; ++best) {}
+            }
+            used[best] = 1;
+            lam[k] = (double)Af[(long long)best * r + best];
+            for (int a = 0; a < r; ++a) coef[(long long)k * r + a] = Uf[(long long)a * r + best];
+        }
+    }
+}
+
 __global__ void std_kernel(const float *__restrict__ V, const double *__restrict__ lam, int rank,
                            const float *__restrict__ B0, long long n, float eps, float *__restrict__ out)
 {
@@ -1008,5 +1099,125 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
                                       "singular Q^T X", "eigenvalues of Omega"};
         return gb_nonfinite(stage[flag_h >= 1 && flag_h <= 4 ? flag_h : 0]);
     }
+    return GBFWI_OK;
+}
+
+extern "C" int gbfwi_lowrank_exact(gbfwi_bfgs *h, int rank, double eps_prior, float *V, double *lambda,
+                                   float *std_out, void *stream)
+{
+    if (!h || !(eps_prior > 0)) return GBFWI_EINVAL;
+    const int k = h->k;
+    if (k < 1 || k > 128) return GBFWI_EINVAL;
+    const int m = 2 * k;
+    if (rank < 1 || rank > m) return GBFWI_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = h->n;
+    const size_t mm = (size_t)m * m;
+    GB_TRY(reserve(h, m, true));
+    GB_TRY(h->ex.ensure((12 * mm + 4 * (size_t)m + 64) * sizeof(double)));
+    GB_TRY(h->E.ensure((size_t)m * n * sizeof(float)));
+    GB_TRY(h->Q.ensure((size_t)m * n * sizeof(float)));
+    GB_TRY(h->V.ensure((size_t)m * n * sizeof(float)));
+    double *G = h->ex.as<double>();
+    double *work = G + mm;                 // 4 mm
+    double *C = work + 4 * mm, *M = C + mm, *P = M + mm, *T = P + mm;
+    double *cA = T + mm, *cR = cA + mm, *cRi = cR + mm;
+    double *d = cRi + mm, *lam = d + m;
+    int *rdev = reinterpret_cast<int *>(lam + m);
+    float *coef = h->coef.as<float>();
+    int *flag = h->flag.as<int>();
+    const float *S = h->S.as<float>(), *BY = h->BY.as<float>();
+    GB_CUDA(cudaMemsetAsync(flag, 0, 16, s));
+
+    // 1. rank-revealing basis of W = [S, B0 Y] (rows s_i, B0 y_i): pivoted
+    //    Cholesky of the column-scaled, compensated-sum Gram matrix, then
+    //    two CholeskyQR passes
+    GB_TRY(atb(h, S, n, k, S, n, k, nullptr, G, m, s, true));
+    GB_TRY(atb(h, S, n, k, BY, n, k, nullptr, G + k, m, s, true));
+    GB_TRY(atb(h, BY, n, k, S, n, k, nullptr, G + (size_t)k * m, m, s, true));
+    GB_TRY(atb(h, BY, n, k, BY, n, k, nullptr, G + (size_t)k * m + k, m, s, true));
+    gram_scale_kernel<<<1, 256, 0, s>>>(G, m, d);
+    GB_LAUNCHED();
+    const size_t ws = (3 * mm + (size_t)m) * sizeof(double);
+    const int use_smem = ws <= 200 * 1024;
+    if (use_smem)
+        GB_CUDA(cudaFuncSetAttribute(gram_pivchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
+    gram_pivchol_kernel<<<1, 512, use_smem ? ws : 0, s>>>(G, m, 1e-4, work, coef, rdev, flag, use_smem);
+    GB_LAUNCHED();
+    int r = 0;
+    GB_CUDA(cudaMemcpyAsync(&r, rdev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (r < 1) return gb_nonfinite("BFGS pairs S, B0 Y are zero or not finite");
+    coef_colscale_kernel<<<grid_n((long long)r * m), 256, 0, s>>>(coef, r, m, d);
+    GB_LAUNCHED();
+    float *Qa = h->E.as<float>(), *Qb = h->Q.as<float>();
+    GB_TRY(combine(h, S, BY, k, m, coef, r, Qa, nullptr, nullptr, 0.f, s));
+    for (int pass = 0; pass < 2; ++pass) {
+        GB_TRY(atb(h, Qa, n, r, Qa, n, r, nullptr, G, r, s));
+        chol_kernel<<<1, 256, 0, s>>>(G, r, 0.0, cA, cR, cRi, coef, flag);
+        GB_LAUNCHED();
+        GB_TRY(combine(h, Qa, nullptr, r, r, coef, r, Qb, nullptr, nullptr, 0.f, s));
+        std::swap(Qa, Qb);                 // Qa: current basis
+    }
+    // 2. C = Q^T W and the middle matrix M of the compact form (gamma = 1):
+    //    B - B0 = W M W^T, M = [[R^-T (D + Y^T B0 Y) R^-1, -R^-T], [-R^-1, 0]]
+    GB_TRY(atb(h, Qa, n, r, S, n, k, nullptr, C, m, s, true));
+    GB_TRY(atb(h, Qa, n, r, BY, n, k, nullptr, C + k, m, s, true));
+    std::vector<double> Mh(mm, 0.0), Ri((size_t)k * k, 0.0);
+    {
+        const int km = h->kmax;
+        for (int c = 0; c < k; ++c)                       // R^-1 by back substitution
+            for (int i = c; i >= 0; --i) {
+                double acc = (i == c) ? 1.0 : 0.0;
+                for (int j = i + 1; j <= c; ++j) acc -= h->SY[(size_t)i * km + j] * Ri[(size_t)j * k + c];
+                Ri[(size_t)i * k + c] = acc / h->SY[(size_t)i * km + i];
+            }
+        std::vector<double> Dm((size_t)k * k), tmp((size_t)k * k, 0.0);
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j)
+                Dm[(size_t)i * k + j] = h->YBY[(size_t)i * km + j] + (i == j ? h->SY[(size_t)i * km + i] : 0.0);
+        for (int i = 0; i < k; ++i)                       // tmp = (D + Y^T B0 Y) R^-1
+            for (int j = 0; j < k; ++j) {
+                double acc = 0.0;
+                for (int l = 0; l < k; ++l) acc += Dm[(size_t)i * k + l] * Ri[(size_t)l * k + j];
+                tmp[(size_t)i * k + j] = acc;
+            }
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) {
+                double acc = 0.0;                         // (R^-T tmp)_ij = sum_l Ri[l][i] tmp[l][j]
+                for (int l = 0; l < k; ++l) acc += Ri[(size_t)l * k + i] * tmp[(size_t)l * k + j];
+                Mh[(size_t)i * m + j] = acc;
+                Mh[(size_t)i * m + k + j] = -Ri[(size_t)j * k + i];     // -R^-T
+                Mh[(size_t)(k + i) * m + j] = -Ri[(size_t)i * k + j];   // -R^-1
+            }
+    }
+    GB_CUDA(cudaMemcpyAsync(M, Mh.data(), mm * sizeof(double), cudaMemcpyHostToDevice, s));
+    // 3. T = C M C^T, its eigenpairs, V = Q U
+    exact_t_kernel<<<1, 512, 0, s>>>(C, M, r, m, P, T);
+    GB_LAUNCHED();
+    const size_t we = ((size_t)r * r + r + 8) * sizeof(double);
+    const int use_smem2 = we <= 200 * 1024;
+    if (use_smem2)
+        GB_CUDA(cudaFuncSetAttribute(eig_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)we));
+    eig_select_kernel<<<1, 512, use_smem2 ? we : 0, s>>>(T, r, rank, work, lam, coef, flag, use_smem2);
+    GB_LAUNCHED();
+    const bool devV = V && gb_is_device_ptr(V);
+    float *Vd = devV ? V : Qb;            // Qb is free
+    GB_TRY(combine(h, Qa, nullptr, r, r, coef, rank, Vd, nullptr, nullptr, 0.f, s));
+    if (std_out) {
+        const bool devS = gb_is_device_ptr(std_out);
+        float *Sd = devS ? std_out : h->V.as<float>();
+        std_kernel<<<grid_n(n), 256, 0, s>>>(Vd, lam, rank, h->B0.as<float>(), n, (float)eps_prior, Sd);
+        GB_LAUNCHED();
+        if (!devS) GB_CUDA(cudaMemcpyAsync(std_out, Sd, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    }
+    if (V && !devV) GB_CUDA(cudaMemcpyAsync(V, Vd, (size_t)rank * n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (lambda)
+        GB_CUDA(cudaMemcpyAsync(lambda, lam, rank * sizeof(double),
+                                gb_is_device_ptr(lambda) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    int flag_h = 0;
+    GB_CUDA(cudaMemcpyAsync(&flag_h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (flag_h) return gb_nonfinite("exact low-rank decomposition of the BFGS pairs");
     return GBFWI_OK;
 }

@@ -174,3 +174,53 @@ def test_lowrank_rank_deficient_probe_block():
     assert np.all(V.cpu().numpy()[2 * k:] == 0.0)
     Bd = ob.dense_inverse(B0, S, Y)
     assert rel(std.cpu().numpy(), np.sqrt(np.diag(Bd))) < 1e-4
+
+
+def test_exact_lowrank_equals_dense_inverse_hessian():
+    """B_{n+1} - B0 has rank <= 2k (compact form): the exact decomposition
+    from a QR of [S, B0 Y] gives the eigenpairs of the dense matrix and the
+    diagonal of the dense B_{n+1} of Eq. 3 (12 x 6 element model size)."""
+    n, k = 3675, 6
+    b, S, Y, B0 = store(n, k)
+    rank = 2 * k
+    lam = torch.zeros(rank, dtype=torch.float64, device=DEV)
+    V = torch.zeros(rank, n, device=DEV)
+    std = torch.zeros(n, device=DEV)
+    b.lowrank_exact(rank, eps_prior=1.0, V=V, lam=lam, std=std)
+    Ue, le = ob.exact_lowrank(S, Y, B0, rank)
+    assert np.allclose(lam.cpu().numpy(), le, rtol=1e-4, atol=1e-6 * np.abs(le).max())
+    Bd = ob.dense_inverse(B0, S, Y)
+    assert rel(std.cpu().numpy(), np.sqrt(np.diag(Bd))) < 1e-4
+    # V diag(lam) V^T equals B_{n+1} - B0 on a probe vector
+    x = np.random.default_rng(1).standard_normal(n)
+    Vg, lg = V.cpu().numpy().astype(np.float64), lam.cpu().numpy()
+    want = (Bd - np.diag(B0)) @ x
+    assert rel(Vg.T @ (lg * (Vg @ x)), want) < 1e-4
+
+
+@pytest.mark.parametrize("n,k,rank", [(30011, 20, 24), (200003, 50, 50)])
+def test_exact_lowrank_matches_algorithm_3_with_full_probing(n, k, rank):
+    """With p >= 2k probes the single-pass randomized SVD is exact (in
+    FP64): the exact decomposition must give the same eigenvalues and
+    posterior std without any probes."""
+    b, S, Y, B0 = store(n, k)
+    lam = torch.zeros(rank, dtype=torch.float64, device=DEV)
+    std = torch.zeros(n, device=DEV)
+    b.lowrank_exact(rank, eps_prior=2.0, lam=lam, std=std)
+    p = 2 * k + 6
+    X = synth.gaussian_block(11, p, n).astype(np.float64)
+    Vr, lr = ob.rsvd_single_pass(ob.probe_block(X, S, Y, B0), X, rank)
+    assert np.allclose(lam.cpu().numpy(), lr, rtol=1e-4, atol=1e-6 * np.abs(lr).max())
+    assert rel(std.cpu().numpy(), ob.posterior_std(Vr, lr, B0, eps=2.0)) < 1e-4
+
+
+def test_exact_and_randomized_agree_on_the_gpu():
+    n, k = 50000, 15
+    b, S, Y, B0 = store(n, k)
+    rank = 2 * k
+    le = torch.zeros(rank, dtype=torch.float64, device=DEV)
+    lr = torch.zeros(rank, dtype=torch.float64, device=DEV)
+    b.lowrank_exact(rank, lam=le)
+    b.lowrank_invhess(2 * k + 8, rank, seed=9, lam=lr)
+    a, c = le.cpu().numpy(), lr.cpu().numpy()
+    assert np.allclose(a, c, rtol=1e-3, atol=1e-5 * np.abs(a).max())
