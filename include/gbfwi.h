@@ -229,8 +229,8 @@ int gbfwi_lowrank_invhess(gbfwi_bfgs *b, const float *X, int p, int rank,
  * (n x 2k) and M = [[R^-T (D + Y^T B0 Y) R^-1, -R^-T], [-R^-1, 0]], so its
  * rank is at most 2k: Q (orthonormal rows spanning the rows of W^T) from
  * pivoted Cholesky of the column-scaled FP64 Gram matrix W^T W (QR with
- * column pivoting; directions below 1e-4 of the largest dropped) and two
- * CholeskyQR passes, then U Lambda U^T = (Q W) M (Q W)^T and V = U^T Q.
+ * column pivoting; directions below 1e-4 of the largest dropped) and shifted
+ * CholeskyQR3, then U Lambda U^T = (Q W) M (Q W)^T and V = U^T Q.
  * Eigenpairs ordered by |lambda| descending; std as in
  * gbfwi_lowrank_invhess.  V: [rank][n] (may be NULL), lambda: [rank] FP64
  * (may be NULL), std: [n] (may be NULL).  1 <= k <= 128 stored pairs,

@@ -493,6 +493,11 @@ __global__ void gram_pivchol_kernel(const double *__restrict__ G, int p, double 
                 int tmp = piv[j];
                 piv[j] = piv[best];
                 piv[best] = tmp;
+                for (int i = 0; i < j; ++i) {      // the finished rows of R follow the swap
+                    double x = R[(long long)i * p + j];
+                    R[(long long)i * p + j] = R[(long long)i * p + best];
+                    R[(long long)i * p + best] = x;
+                }
                 s_d = sqrt(bv);
                 R[(long long)j * p + j] = s_d;
                 s_go = 1;
@@ -1030,8 +1035,7 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
     GB_TRY(apply_dev(h, Xd, p, E, 1.0, 1, s, true));
     // 2. rank-revealing basis of E: pivoted Cholesky of its FP64 Gram matrix,
     //    rows kept while their residual norm is >= 1e-4 of the largest (what an
-    //    FP32 block resolves), then one CholeskyQR pass to restore
-    //    orthonormality in FP32
+    //    FP32 block resolves)
     const size_t pp = (size_t)p * p;
     double *G = h->small.as<double>() + small_apply_doubles(h, p);
     double *A = G + pp, *R2 = A + pp, *Rinv = R2 + pp, *QE = Rinv + pp, *QX = QE + pp;
@@ -1055,19 +1059,20 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
     GB_CUDA(cudaStreamSynchronize(s));
     if (r < 1) return gb_nonfinite("probe block E = (B - B0) X is zero or not finite");
     GB_TRY(combine(h, E, nullptr, p, p, coef, r, Q, nullptr, nullptr, 0.f, s));   // Q1 [r][n] in Q
-    GB_TRY(atb(h, Q, n, r, Q, n, r, nullptr, G, r, s));          // Q1 nearly orthonormal: FP32 sums
-    chol_kernel<<<1, 256, 0, s>>>(G, r, 0.0, A, R2, Rinv, coef, flag);
-    GB_LAUNCHED();
-    float *Qf = h->V.as<float>();
+    // shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa
+    // 2020): Q1 is orthonormal only up to its FP32 rounding times cond(R11),
+    // and its FP32 Gram matrix may then miss definiteness; the first pass
+    // adds 1e-5 tr(G) to the diagonal (well above the Gram's rounding), the
+    // two unshifted passes make the rows orthonormal to FP32 rounding
     GB_TRY(h->V.ensure((size_t)p * n * sizeof(float)));
-    Qf = h->V.as<float>();
-    GB_TRY(combine(h, Q, nullptr, r, r, coef, r, Qf, nullptr, nullptr, 0.f, s));  // Q [r][n]
-    // second CholeskyQR pass (CholeskyQR2): the rounding of the first leaves
-    // Q orthonormal only to ~eps cond(R11), which Algorithm 3 amplifies
-    GB_TRY(atb(h, Qf, n, r, Qf, n, r, nullptr, G, r, s));
-    chol_kernel<<<1, 256, 0, s>>>(G, r, 0.0, A, R2, Rinv, coef, flag);
-    GB_LAUNCHED();
-    GB_TRY(combine(h, Qf, nullptr, r, r, coef, r, Q, nullptr, nullptr, 0.f, s));
+    float *Qf = h->V.as<float>();
+    for (int pass = 0; pass < 3; ++pass) {
+        GB_TRY(atb(h, Q, n, r, Q, n, r, nullptr, G, r, s));
+        chol_kernel<<<1, 256, 0, s>>>(G, r, pass == 0 ? 1e-5 : 0.0, A, R2, Rinv, coef, flag);
+        GB_LAUNCHED();
+        GB_TRY(combine(h, Q, nullptr, r, r, coef, r, Qf, nullptr, nullptr, 0.f, s));
+        std::swap(Q, Qf);                 // Q: current basis; Qf: free
+    }
     std::swap(Q, Qf);                     // Qf: the basis; Q: free
     // 3. Q^T E, Q^T X ; Omega by least squares ; eigenpairs
     GB_TRY(atb(h, Qf, n, r, E, n, p, nullptr, QE, p, s, true));
@@ -1131,7 +1136,7 @@ extern "C" int gbfwi_lowrank_exact(gbfwi_bfgs *h, int rank, double eps_prior, fl
 
     // 1. rank-revealing basis of W = [S, B0 Y] (rows s_i, B0 y_i): pivoted
     //    Cholesky of the column-scaled, compensated-sum Gram matrix, then
-    //    two CholeskyQR passes
+    //    shifted CholeskyQR3
     GB_TRY(atb(h, S, n, k, S, n, k, nullptr, G, m, s, true));
     GB_TRY(atb(h, S, n, k, BY, n, k, nullptr, G + k, m, s, true));
     GB_TRY(atb(h, BY, n, k, S, n, k, nullptr, G + (size_t)k * m, m, s, true));
@@ -1152,9 +1157,9 @@ extern "C" int gbfwi_lowrank_exact(gbfwi_bfgs *h, int rank, double eps_prior, fl
     GB_LAUNCHED();
     float *Qa = h->E.as<float>(), *Qb = h->Q.as<float>();
     GB_TRY(combine(h, S, BY, k, m, coef, r, Qa, nullptr, nullptr, 0.f, s));
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < 3; ++pass) {   // shifted CholeskyQR3, as in gbfwi_lowrank_invhess
         GB_TRY(atb(h, Qa, n, r, Qa, n, r, nullptr, G, r, s));
-        chol_kernel<<<1, 256, 0, s>>>(G, r, 0.0, cA, cR, cRi, coef, flag);
+        chol_kernel<<<1, 256, 0, s>>>(G, r, pass == 0 ? 1e-5 : 0.0, cA, cR, cRi, coef, flag);
         GB_LAUNCHED();
         GB_TRY(combine(h, Qa, nullptr, r, r, coef, r, Qb, nullptr, nullptr, 0.f, s));
         std::swap(Qa, Qb);                 // Qa: current basis

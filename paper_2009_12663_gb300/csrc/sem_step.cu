@@ -338,8 +338,16 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
             }
         }
     }
-    const int e = threadIdx.x;
-    const int elx = e % (TX + 1), elz = e / (TX + 1);
+    // Element of this thread.  A warp holds R = 32 / (TX + 1) rows of the
+    // extended tile, all of one row parity (rows r, r + 2, ...), so its
+    // elements take only two of the four colours below and it runs the
+    // accumulation body in two of the four passes (rows of one half-warp
+    // stay contiguous: the same shared-memory bank pattern as row order).
+    constexpr int R = 32 / (TX + 1);
+    static_assert(R >= 1 && 32 % (TX + 1) == 0 && (TZ + 1) % (2 * R) == 0, "parity-grouped element rows");
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int elx = lane % (TX + 1);
+    const int elz = (wid >> 1) * 2 * R + (wid & 1) + 2 * (lane / (TX + 1));
     const bool evalid = (ex0 - 1 + elx >= 0) && (ez0 - 1 + elz >= 0) && (ex0 - 1 + elx < a.nex) &&
                         (ez0 - 1 + elz < a.nez);
     const int ebase = 4 * elz * NWXP + 4 * elx;

@@ -11,7 +11,9 @@ quasi-Newton step; a scaled first step) and the model bookkeeping are small
 vector operations done with torch; they are not part of the timed path.
 
 Parameters are (rho, vp, vs) on the node grid; `invert` selects which of them
-are unknowns (the paper's Marmousi runs keep rho fixed).
+are unknowns (the paper's Marmousi runs keep rho fixed).  The first step (and
+a restart) moves the model by step0 max|m| at the 99.9th percentile of the
+direction's magnitude.
 """
 from __future__ import annotations
 
@@ -78,6 +80,16 @@ def preconditioner(mesh: Mesh, shot_ids, m0: torch.Tensor, kind: int, sigma: flo
     return B0
 
 
+def robust_max(v: torch.Tensor, q: float = 0.999) -> float:
+    """The q-quantile of |v| (on at most ~1M evenly spaced samples): the
+    scale of a search direction without its few largest entries (a single
+    spike of the preconditioner would otherwise set the first step)."""
+    a = v.abs().reshape(-1)
+    if a.numel() > 1_000_000:
+        a = a[:: (a.numel() + 999_999) // 1_000_000]
+    return float(torch.quantile(a.float(), q))
+
+
 def fwi(problem: Problem, m0: torch.Tensor, iterations: int, B0=None, memory=None, step0=0.02,
         c1=1e-4, max_backtracks=8, callback=None, pairs_out=None):
     """Run (L-)BFGS.  Returns (model, history, store); `store` is the
@@ -105,7 +117,7 @@ def fwi(problem: Problem, m0: torch.Tensor, iterations: int, B0=None, memory=Non
         k = cur.count
         if k == 0:
             p = -(b0 * gv)
-            alpha = step0 * float(m[mask.to(m.device)].abs().max()) / float(p.abs().max())
+            alpha = step0 * float(m[mask.to(m.device)].abs().max()) / robust_max(p)
         else:
             s_last, y_last = pairs[-1]
             # gamma_k of Algorithm 1 weighted by the preconditioner: the paper's
@@ -120,7 +132,7 @@ def fwi(problem: Problem, m0: torch.Tensor, iterations: int, B0=None, memory=Non
         if gtp >= 0:                                   # not a descent direction: restart
             p = -(b0 * gv)
             gtp = float((gv * p).sum())
-            alpha = step0 * float(m[mask.to(m.device)].abs().max()) / float(p.abs().max())
+            alpha = step0 * float(m[mask.to(m.device)].abs().max()) / robust_max(p)
         accepted = False
         for _ in range(max_backtracks):
             m_try = clamp_model(m + alpha * unpack(p, mask, m))

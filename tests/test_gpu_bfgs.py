@@ -224,3 +224,33 @@ def test_exact_and_randomized_agree_on_the_gpu():
     b.lowrank_invhess(2 * k + 8, rank, seed=9, lam=lr)
     a, c = le.cpu().numpy(), lr.cpu().numpy()
     assert np.allclose(a, c, rtol=1e-3, atol=1e-5 * np.abs(a).max())
+
+
+def test_lowrank_ill_conditioned_history():
+    """Nearly parallel model updates (as in a converging inversion) make the
+    probe block E ill-conditioned; the rank-revealing basis must pivot
+    correctly and the resolved eigenvalues match Algorithm 3 in FP64 with
+    the same (device Philox) probes."""
+    n, k, seed = 20000, 12, 2020
+    rng = np.random.default_rng(31)
+    A = rng.uniform(1.0, 10.0, n)
+    base = rng.standard_normal(n) * 1e-2
+    S = np.stack([base + 10.0 ** (-0.4 * i) * 1e-2 * rng.standard_normal(n) for i in range(k)])
+    Y = S * A + 1e-6 * rng.standard_normal((k, n))
+    B0 = (1.0 / A) * rng.uniform(0.5, 2.0, n)
+    S, Y, B0 = S.astype(np.float32), Y.astype(np.float32), B0.astype(np.float32)
+    b = gb.Bfgs(n, k, t32(B0))
+    for i in range(k):
+        b.update(t32(S[i]), t32(Y[i]))
+    p = rank = k
+    lam = torch.zeros(rank, dtype=torch.float64, device=DEV)
+    b.lowrank_invhess(p, rank, seed=seed, eps_prior=1.0, lam=lam)
+    X = philox.gaussian_block(seed, p, n)
+    E = ob.probe_block(X, S.astype(np.float64), Y.astype(np.float64), B0.astype(np.float64))
+    sv = np.linalg.svd(E, compute_uv=False)
+    assert sv[-1] / sv[0] < 1e-3          # the case this test is about
+    _, lr = ob.rsvd_single_pass(E, X, rank)
+    lg = lam.cpu().numpy()
+    big = np.abs(lr) >= 1e-3 * np.abs(lr).max()
+    assert np.allclose(lg[big], lr[big], rtol=1e-2), (lg, lr)
+    assert np.all(np.abs(lg[~big]) <= 2e-3 * np.abs(lr).max())
