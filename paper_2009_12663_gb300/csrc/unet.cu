@@ -44,6 +44,7 @@ namespace {
 constexpr int GBK = 32;        // k extent of a staged tile
 constexpr int GPAD = 8;        // bf16 padding per shared row (ldmatrix rows on distinct banks)
 constexpr int GTHREADS = 256;  // 8 warps, each owning a 32 x 32 block of C
+constexpr int GSTAGES = 3;     // cp.async pipeline depth (tiles in flight + 1)
 
 struct GemmArgs {
     const bf16 *A;
@@ -154,8 +155,9 @@ __global__ void __launch_bounds__(GTHREADS) gemm_bf16_kernel(const GemmArgs g)
 {
     using T = GemmTile<BM, BN, A_KM, B_NK>;
     static_assert((BM / 32) * (BN / 32) == GTHREADS / 32, "warp layout");
-    __shared__ __align__(16) bf16 As[2][T::AE];
-    __shared__ __align__(16) bf16 Bs[2][T::BE];
+    extern __shared__ __align__(16) unsigned char gsm[];   // GSTAGES x (A tile, B tile)
+    bf16 *As0 = reinterpret_cast<bf16 *>(gsm);
+    bf16 *Bs0 = As0 + GSTAGES * T::AE;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wm = warp % (BM / 32), wn = warp / (BM / 32);
@@ -171,13 +173,33 @@ __global__ void __launch_bounds__(GTHREADS) gemm_bf16_kernel(const GemmArgs g)
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[i][j][v] = 0.f;
 
-    int st = 0;
-    if (kbeg < kend) gemm_stage<BM, BN, A_KM, B_NK>(g, As[0], Bs[0], m0, n0, kbeg, kend);
-    for (int k0 = kbeg; k0 < kend; k0 += GBK) {
-        asm volatile("cp.async.wait_group 0;\n" ::);
+    // GSTAGES-deep cp.async pipeline: tiles it+1 .. it+GSTAGES-1 are in flight
+    // while tile it is consumed; every iteration commits one group (empty
+    // past the end) so that wait_group GSTAGES-2 always means "tile it landed"
+#pragma unroll
+    for (int sidx = 0; sidx < GSTAGES - 1; ++sidx) {
+        const int kk0 = kbeg + sidx * GBK;
+        if (kk0 < kend)
+            gemm_stage<BM, BN, A_KM, B_NK>(g, As0 + sidx * T::AE, Bs0 + sidx * T::BE, m0, n0, kk0, kend);
+        else
+            asm volatile("cp.async.commit_group;\n" ::);
+    }
+    int it = 0;
+    for (int k0 = kbeg; k0 < kend; k0 += GBK, ++it) {
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(GSTAGES - 2));
         __syncthreads();
-        if (k0 + GBK < kend) gemm_stage<BM, BN, A_KM, B_NK>(g, As[st ^ 1], Bs[st ^ 1], m0, n0, k0 + GBK, kend);
-        const bf16 *as = As[st], *bs = Bs[st];
+        {
+            // refill the slot consumed in the previous iteration (all threads
+            // are past it: the barrier above)
+            const int kn = k0 + (GSTAGES - 1) * GBK;
+            const int slot = (it + GSTAGES - 1) % GSTAGES;
+            if (kn < kend)
+                gemm_stage<BM, BN, A_KM, B_NK>(g, As0 + slot * T::AE, Bs0 + slot * T::BE, m0, n0, kn, kend);
+            else
+                asm volatile("cp.async.commit_group;\n" ::);
+        }
+        const int cur = it % GSTAGES;
+        const bf16 *as = As0 + cur * T::AE, *bs = Bs0 + cur * T::BE;
 #pragma unroll
         for (int kk = 0; kk < GBK; kk += 16) {
             unsigned a[2][4], b[4][2];
@@ -217,8 +239,8 @@ __global__ void __launch_bounds__(GTHREADS) gemm_bf16_kernel(const GemmArgs g)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j][0], b[j][1]);
         }
-        st ^= 1;
     }
+    asm volatile("cp.async.wait_group 0;\n" ::);
 
     // epilogue: thread holds rows g, g+8 and columns 2t, 2t+1 of each 16 x 8 tile
     const int gr = lane >> 2, tc = (lane & 3) * 2;
@@ -611,7 +633,17 @@ int launch_gemm(const GemmArgs &g, cudaStream_t s)
 {
     constexpr int BN = 256 * 32 / BM;
     dim3 grid((unsigned)((g.N + BN - 1) / BN), (unsigned)((g.M + BM - 1) / BM), (unsigned)g.splits);
-    gemm_bf16_kernel<BM, BN, AK, BK><<<grid, GTHREADS, 0, s>>>(g);
+    using T = GemmTile<BM, BN, AK, BK>;
+    constexpr size_t smem = (size_t)GSTAGES * (T::AE + T::BE) * sizeof(bf16);
+    static bool attr_done[64] = {};      // per device ordinal
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+        GB_CUDA(cudaFuncSetAttribute(gemm_bf16_kernel<BM, BN, AK, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        attr_done[dev] = true;
+    }
+    gemm_bf16_kernel<BM, BN, AK, BK><<<grid, GTHREADS, smem, s>>>(g);
     GB_LAUNCHED();
     return GBFWI_OK;
 }
