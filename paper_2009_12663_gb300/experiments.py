@@ -9,7 +9,8 @@ Prints one JSON document: per variant the relative data misfit and the
 relative model misfit (vp, vs) per iteration, iterations to halve the misfit,
 wall time; for the P4 run the leading eigenvalues of the retrieved
 B_{n+1} - B0, the posterior std of vp / vs and its correlation with the
-absolute error of the inverted model.
+absolute error of the inverted model, and the data misfit along
+perturbations shaped by the std maps (Appendix C) next to random ones.
 """
 from __future__ import annotations
 
@@ -29,9 +30,9 @@ if ROOT not in sys.path:
 import synth  # noqa: E402
 
 from . import Mesh  # noqa: E402
-from .fwi import Problem, fwi, model_misfit, preconditioner  # noqa: E402
+from .fwi import Problem, clamp_model, fwi, model_misfit, preconditioner  # noqa: E402
 
-__all__ = ["build", "run", "learned_comparison"]
+__all__ = ["build", "run", "learned_comparison", "misfit_scan"]
 
 
 def build(nex=80, nez=20, h=50.0, nshot=8, f0=8.0, nt=3000, seed=11, smooth=250.0, device="cuda"):
@@ -90,7 +91,35 @@ def run(iterations=15, sigma=100.0, rank=None):
     out["uq_P4"] = {"pairs": k, "probes": p, "rank": r, "eigenvalues": lam.cpu().numpy().tolist(),
                     "std_mean_vp": float(stdm[0].mean()), "std_mean_vs": float(stdm[1].mean()),
                     "corr_std_vs_abs_error": {"vp": corr[0], "vs": corr[1]}}
+    out["uq_misfit_scan"] = misfit_scan(prob, m_inv, torch.tensor(stdm, device=true.device), mask)
     return out
+
+
+def misfit_scan(prob, m_inv, std_maps, mask, vmax=250.0, alphas=(-2, -1.5, -1, -0.5, 0, 0.5, 1, 1.5, 2), seed=5):
+    """Appendix C in kind: the data misfit along m_inv + alpha m_pert, with
+    m_pert the posterior std map of each inverted parameter scaled to a
+    maximum of vmax m/s, next to a smooth random perturbation of the same
+    maximum (Gaussian bumps).  Misfits relative to the one at m_inv."""
+    mk = mask.to(m_inv.device)
+    pert = torch.zeros_like(m_inv)
+    pert[mk] = std_maps / std_maps.amax(dim=(1, 2), keepdim=True) * vmax
+    nz, nx = m_inv.shape[1:]
+    rng = np.random.default_rng(seed)
+    zz, xx = np.meshgrid(np.arange(nz), np.arange(nx), indexing="ij")
+    rnd = torch.zeros_like(m_inv)
+    for c in np.nonzero(mask.numpy())[0]:
+        f = np.zeros((nz, nx))
+        for _ in range(12):
+            cz, cx, w = rng.uniform(0, nz), rng.uniform(0, nx), rng.uniform(6, 20)
+            f += rng.standard_normal() * np.exp(-((zz - cz) ** 2 + (xx - cx) ** 2) / (2 * w * w))
+        rnd[c] = torch.tensor(f / np.abs(f).max() * vmax, dtype=m_inv.dtype, device=m_inv.device)
+    f0 = prob.misfit(clamp_model(m_inv))
+    scan = {"alpha": list(alphas), "std_pert": [], "random_pert": []}
+    for a in alphas:
+        scan["std_pert"].append(prob.misfit(clamp_model(m_inv + a * pert)) / f0)
+        scan["random_pert"].append(prob.misfit(clamp_model(m_inv + a * rnd)) / f0)
+    scan["vmax_m_per_s"] = vmax
+    return scan
 
 
 def main():
