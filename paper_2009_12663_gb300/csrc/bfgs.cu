@@ -11,9 +11,16 @@
 //
 // Layout: vectors are rows, S / Y / B0Y are [kmax][n] FP32, blocks X / E / Q /
 // V are [p][n] FP32.  The n-long work is (a) split-K products A B^T with a
-// deterministic FP64 reduction over the splits and (b) row combinations
-// out = coef * rows; the small matrices (middle matrix, Cholesky factors,
-// Omega and its eigendecomposition) are FP64 and solved in one CTA.
+// deterministic FP64 reduction over the splits (FP32 or compensated sums
+// within a split) and (b) row combinations out = coef * rows; the small
+// matrices (middle matrix, pivoted and plain Cholesky factors, the solve
+// for Omega) are FP64 in one CTA, and the small symmetric eigenproblems run
+// as FP32 block Jacobi sweeps in one CTA.
+//
+// The low-rank part (Algorithm 3, gbfwi_lowrank_invhess): E = (B - B0) X,
+// a rank-revealing orthonormal basis Q of E (pivoted Cholesky of E E^T,
+// shifted CholeskyQR3), Omega (Q X) = Q E by least squares, Omega = U L U^T,
+// V = U^T Q.  gbfwi_lowrank_exact takes Q from [S, B0 Y] instead of probes.
 
 #include <algorithm>
 #include <cmath>
@@ -305,7 +312,8 @@ __global__ void middle_kernel(const double *__restrict__ T, const double *__rest
 
 // Cholesky G + shift tr(G) I = R^T R (R upper, p x p, FP64, in global
 // scratch), then coef = R^-T (lower) as FP32 for the row combination
-// Q = R^-T E (one CholeskyQR pass; shift = 0 unless a caller regularises).
+// Q = R^-T E (one CholeskyQR pass; the first pass of shifted CholeskyQR3
+// passes shift > 0).
 __global__ void chol_kernel(const double *__restrict__ G, int p, double shift, double *__restrict__ A,
                             double *__restrict__ R, double *__restrict__ Rinv, float *__restrict__ coef,
                             int *__restrict__ flag)
