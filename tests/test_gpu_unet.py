@@ -191,3 +191,21 @@ def test_fallback_uses_computed_map_when_prediction_is_off(small_mesh):
     ref = torch.zeros_like(mdl)
     m.precond_from_hessian(H, 100.0, 1.0, ref)
     assert torch.equal(B0, ref)
+
+
+def test_full_size_forward_on_a_window():
+    """The network at its full shape (4 levels, 32 channels, 256 x 1024)
+    against the oracle on sampled outputs: an output pixel depends only on
+    its receptive field (under 96 pixels wide here: 3x3 convolutions at
+    strides 1-8 and pooling grids aligned to multiples of 8), so the oracle
+    on the full-height window of columns [384, 640) gives the exact network
+    output on its central columns [480, 544)."""
+    levels, base, H, W = 4, 32, 256, 1024
+    net, params, x = setup_net(levels, base, H, W, seed=41)
+    y = torch.zeros(3, H, W, device=DEV)
+    net.forward(torch.tensor(x, device=DEV), y)
+    x0, x1, c0, c1 = 384, 640, 480, 544
+    ref, _ = ou.forward(params, x[:, :, x0:x1].astype(np.float64), levels, bf16_on=True)
+    got = y.cpu().numpy()[:, :, c0:c1]
+    want = ref[:, :, c0 - x0:c1 - x0]
+    assert rel(got, want) < 2e-2, rel(got, want)
