@@ -10,7 +10,10 @@ each stream replays its time loops as CUDA graphs):
   bfgs_update -> lowrank_invhess (50-pair store, 60 probes, rank 50,
   n = 3 x 382,441).
 metric: GLL-point-updates/s = 2 * shots * N_glob * nt / step time; the line
-also reports s per gradient and s per rank-k UQ.
+also reports s per gradient and s per rank-k UQ.  After the timed region it
+times, outside `value`, the exact low-rank decomposition of the same store
+(`uq_exact`) and the learned-preconditioner U-Net at 256 x 1024
+(`learned_preconditioner`, skipped with --no-unet).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank runs its own 24 shots (weak scaling); rank 0
