@@ -137,7 +137,7 @@ def main():
 
 
 
-def learned_comparison(n_train=48, n_test=4, nt=3000, img=(256, 1024), steps=600, iterations=8, seed0=1000,
+def learned_comparison(n_train=48, n_test=4, nt=3000, img=(256, 1024), steps=2000, iterations=8, seed0=1000,
                        device="cuda"):
     """The learned preconditioner in kind of its intended use, on the
     340 x 70 element Marmousi-shaped mesh (24 shots, 5 Hz, `nt` steps):
@@ -168,7 +168,7 @@ def learned_comparison(n_train=48, n_test=4, nt=3000, img=(256, 1024), steps=600
     t_pairs = time.perf_counter() - t0
     net = Unet(levels=4, base=32, cin=5, cout=3, height=img[0], width=img[1])
     lp = L.LearnedPreconditioner(net, seed=1)
-    t_train = lp.fit(X[:n_train], T[:n_train], steps=steps, lr=1e-3, batch=4, seed=2, lr_decay=0.997)
+    t_train = lp.fit(X[:n_train], T[:n_train], steps=steps, lr=1e-3, batch=4, seed=2, lr_decay=0.999)
     errs = []
     for i in range(n_train, n_train + n_test):
         Hc = L.computed_map(m, models[i], ids)
