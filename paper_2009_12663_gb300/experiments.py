@@ -3,7 +3,7 @@ synthetic models (Section 3: BFGS vs L-BFGS(5), preconditioners P1-P4,
 RSVD uncertainty maps compared with the true model error).
 
     python -m paper_2009_12663_gb300.experiments [--iterations 15] [--out result.json]
-    python -m paper_2009_12663_gb300.experiments --learned [--out result.json]
+    python -m paper_2009_12663_gb300.experiments --learned [--train-pairs 48] [--train-steps 2000] [--out result.json]
 
 Prints one JSON document: per variant the relative data misfit and the
 relative model misfit (vp, vs) per iteration, iterations to halve the misfit,
@@ -126,9 +126,15 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--iterations", type=int, default=15)
     ap.add_argument("--learned", action="store_true", help="run the learned-preconditioner comparison")
+    ap.add_argument("--train-pairs", type=int, default=48, help="training pairs of the learned comparison")
+    ap.add_argument("--train-steps", type=int, default=2000, help="Adam steps of the learned comparison")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
-    res = learned_comparison() if a.learned else run(a.iterations)
+    if a.learned:
+        decay = 0.135 ** (1.0 / max(1, a.train_steps))      # learning rate 1e-3 -> 1.35e-4 over the run
+        res = learned_comparison(n_train=a.train_pairs, steps=a.train_steps, lr_decay=decay)
+    else:
+        res = run(a.iterations)
     txt = json.dumps(res)
     print(txt)
     if a.out:
@@ -138,7 +144,7 @@ def main():
 
 
 def learned_comparison(n_train=48, n_test=4, nt=3000, img=(256, 1024), steps=2000, iterations=8, seed0=1000,
-                       device="cuda"):
+                       device="cuda", lr_decay=0.999):
     """The learned preconditioner in kind of its intended use, on the
     340 x 70 element Marmousi-shaped mesh (24 shots, 5 Hz, `nt` steps):
     train the U-Net on P4 maps the method computes for seeded models, then
@@ -168,7 +174,7 @@ def learned_comparison(n_train=48, n_test=4, nt=3000, img=(256, 1024), steps=200
     t_pairs = time.perf_counter() - t0
     net = Unet(levels=4, base=32, cin=5, cout=3, height=img[0], width=img[1])
     lp = L.LearnedPreconditioner(net, seed=1)
-    t_train = lp.fit(X[:n_train], T[:n_train], steps=steps, lr=1e-3, batch=4, seed=2, lr_decay=0.999)
+    t_train = lp.fit(X[:n_train], T[:n_train], steps=steps, lr=1e-3, batch=4, seed=2, lr_decay=lr_decay)
     errs = []
     for i in range(n_train, n_train + n_test):
         Hc = L.computed_map(m, models[i], ids)
