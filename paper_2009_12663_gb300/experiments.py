@@ -3,7 +3,8 @@ synthetic models (Section 3: BFGS vs L-BFGS(5), preconditioners P1-P4,
 RSVD uncertainty maps compared with the true model error).
 
     python -m paper_2009_12663_gb300.experiments [--iterations 15] [--out result.json]
-    python -m paper_2009_12663_gb300.experiments --learned [--train-pairs 48] [--train-steps 2000] [--out result.json]
+    python -m paper_2009_12663_gb300.experiments --learned [--train-pairs 48] [--train-steps 2000]
+                                                 [--lr-decay 0.999] [--out result.json]
 
 Prints one JSON document: per variant the relative data misfit and the
 relative model misfit (vp, vs) per iteration, iterations to halve the misfit,
@@ -128,11 +129,11 @@ def main():
     ap.add_argument("--learned", action="store_true", help="run the learned-preconditioner comparison")
     ap.add_argument("--train-pairs", type=int, default=48, help="training pairs of the learned comparison")
     ap.add_argument("--train-steps", type=int, default=2000, help="Adam steps of the learned comparison")
+    ap.add_argument("--lr-decay", type=float, default=0.999, help="learning-rate factor per Adam step")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     if a.learned:
-        decay = 0.135 ** (1.0 / max(1, a.train_steps))      # learning rate 1e-3 -> 1.35e-4 over the run
-        res = learned_comparison(n_train=a.train_pairs, steps=a.train_steps, lr_decay=decay)
+        res = learned_comparison(n_train=a.train_pairs, steps=a.train_steps, lr_decay=a.lr_decay)
     else:
         res = run(a.iterations)
     txt = json.dumps(res)
