@@ -18,8 +18,11 @@
  *     arguments are written only on success.  gbfwi_strerror() names a code.
  *   - Arrays: the caller owns every array argument.  Each array may be host
  *     or device memory; the library looks at the pointer (CUDA pointer
- *     attributes).  Host arrays are staged through library-owned device
- *     buffers and the call returns only after its host outputs are written;
+ *     attributes).  Device arrays must belong to the device that is current
+ *     during the call (or be managed memory): another GPU's memory is
+ *     rejected with GBFWI_EINVAL.  Host arrays are staged through
+ *     library-owned device buffers and the call returns only after its host
+ *     outputs are written;
  *     with device arrays the work is queued on `stream` (a cudaStream_t, or
  *     NULL for the legacy default stream) and the call returns once it is
  *     queued, except where an entry point says it synchronises.
@@ -347,10 +350,15 @@ int gbfwi_precond_from_hessian(gbfwi_mesh *mesh, const float *H, double smooth_s
  *             [nshot][nrec][2][nt] seismograms of gbfwi_forward);
  *   misfit:   host array [nshot] FP64, written only on success.
  * nshot <= GBFWI_NOALLOC_MAX_SHOTS, else GBFWI_ESCRATCH.  The call allocates
- * nothing and synchronises the stream.  The first call on a device looks up
- * the scratch array's device address; make that first call before any stream
- * capture.  All calls share one scratch array per device and it keeps the
- * last call's partial sums: calls that overlap on the GPU race.
+ * nothing, copies its results to host memory and synchronises the stream, so
+ * it cannot be called on a stream that is being captured into a CUDA graph
+ * (-> EINVAL).  The first call on a device looks up the scratch array's
+ * device address; under CUDA's default lazy module loading that first call
+ * is also where the library's device code and the array (about 130 KB) are
+ * loaded onto that device, so make it before the memory is handed to the
+ * caller's own pool (or load modules eagerly, CUDA_MODULE_LOADING=EAGER).
+ * All calls share one scratch array per device and it keeps the last call's
+ * partial sums: calls that overlap on the GPU race.
  * -> EINVAL, ESCRATCH, ENONFINITE, ECUDA. */
 int gbfwi_misfit_noalloc(const float *syn, const float *obs, int nshot, long long samples_per_shot,
                          double dt, double *misfit, void *stream);

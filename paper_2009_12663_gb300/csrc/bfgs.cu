@@ -919,6 +919,7 @@ int apply_dev(gbfwi_bfgs *h, const float *Xd, int p, float *Zd, double gamma, in
 extern "C" int gbfwi_bfgs_create(long long n, int kmax, const float *B0, gbfwi_bfgs **out)
 {
     if (n < 1 || kmax < 1 || kmax > 4096 || !B0 || !out) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(B0));
     gbfwi_bfgs *h = new (std::nothrow) gbfwi_bfgs();
     if (!h) return GBFWI_ENOMEM;
     h->n = n;
@@ -954,6 +955,7 @@ extern "C" int gbfwi_bfgs_count(const gbfwi_bfgs *h) { return h ? h->k : GBFWI_E
 extern "C" int gbfwi_bfgs_update(gbfwi_bfgs *h, const float *s_, const float *y_, void *stream)
 {
     if (!h || !s_ || !y_) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(s_, y_));
     if (h->k >= h->kmax) return GBFWI_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const long long n = h->n;
@@ -1000,6 +1002,7 @@ extern "C" int gbfwi_bfgs_apply(gbfwi_bfgs *h, const float *X, int p, float *Z, 
                                 void *stream)
 {
     if (!h || !X || !Z || p < 1 || p > 256 || !(gamma > 0)) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(X, Z));
     cudaStream_t s = (cudaStream_t)stream;
     const long long n = h->n;
     const float *Xd;
@@ -1023,6 +1026,7 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
                                      double eps_prior, float *V, double *lambda, float *std_out, void *stream)
 {
     if (!h || p < 1 || p > 256 || rank < 1 || rank > p || !(eps_prior > 0)) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(X, V, lambda, std_out));
     cudaStream_t s = (cudaStream_t)stream;
     const long long n = h->n;
     const float *Xd;
@@ -1119,6 +1123,7 @@ extern "C" int gbfwi_lowrank_exact(gbfwi_bfgs *h, int rank, double eps_prior, fl
                                    float *std_out, void *stream)
 {
     if (!h || !(eps_prior > 0)) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(V, lambda, std_out));
     const int k = h->k;
     if (k < 1 || k > 128) return GBFWI_EINVAL;
     const int m = 2 * k;

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "gbfwi.h"
+#include "ptrclass.h"
 
 #define GB_NG 5
 
@@ -59,8 +60,21 @@ struct DevBuf {
     DevBuf &operator=(const DevBuf &) = delete;
 };
 
-// true when ptr is device (or managed) memory of the current context
+// GB_PTR_HOST, GB_PTR_LOCAL or GB_PTR_FOREIGN for a caller's array (NULL is host)
+int gb_ptr_class(const void *ptr);
+// true when ptr is memory of the current device (or managed memory)
 bool gb_is_device_ptr(const void *ptr);
+
+// GBFWI_OK when every given array is host memory or memory of the current
+// device; GBFWI_EINVAL when one lives on another device (the kernels would
+// fault on it instead of returning an error)
+inline int gb_check_local() { return GBFWI_OK; }
+template <class P, class... Rest>
+int gb_check_local(P p, Rest... rest)
+{
+    if (gb_ptr_class(static_cast<const void *>(p)) == GB_PTR_FOREIGN) return GBFWI_EINVAL;
+    return gb_check_local(rest...);
+}
 
 // ---------------------------------------------------------------------------
 // element tiles

@@ -89,16 +89,27 @@ void DevBuf::release()
     bytes = 0;
 }
 
-bool gb_is_device_ptr(const void *ptr)
+static_assert(cudaMemoryTypeUnregistered == GB_MEMTYPE_UNREGISTERED && cudaMemoryTypeHost == GB_MEMTYPE_HOST &&
+                  cudaMemoryTypeDevice == GB_MEMTYPE_DEVICE && cudaMemoryTypeManaged == GB_MEMTYPE_MANAGED,
+              "memory type values of ptrclass.h");
+
+int gb_ptr_class(const void *ptr)
 {
-    if (!ptr) return false;
+    if (!ptr) return GB_PTR_HOST;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return GB_PTR_HOST;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        cur = -1;
+    }
+    return gb_classify_pointer((int)at.type, at.device, cur);
 }
+
+bool gb_is_device_ptr(const void *ptr) { return gb_ptr_class(ptr) == GB_PTR_LOCAL; }
 
 extern "C" const char *gbfwi_strerror(int code)
 {
@@ -538,6 +549,7 @@ extern "C" int gbfwi_set_model(gbfwi_mesh *m, const float *rho, const float *vp,
                                void *stream)
 {
     if (!m || !rho || !vp || !vs) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(rho, vp, vs));
     cudaStream_t s = (cudaStream_t)stream;
     const size_t N = (size_t)m->nx * m->nz;
     std::vector<float> h(3 * N);

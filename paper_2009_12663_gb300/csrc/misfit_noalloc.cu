@@ -10,9 +10,15 @@
 // a fixed, file-scope device array instead of a library work buffer.
 //
 // The array is sized for at most GBFWI_NOALLOC_MAX_SHOTS shots and exists on
-// every GPU that loads the library until the process exits (about 130 KB).
-// All calls share it and it keeps the contents of the last call: calls whose
-// work overlaps on the GPU (different streams, or threads) race on it.
+// every GPU that loads the library's device code until the process exits
+// (about 130 KB).  With CUDA's default lazy module loading that device code,
+// and with it the array, is loaded on a device by the first call there (the
+// symbol lookup below); that first call is the one that can reserve memory,
+// so a caller whose pool takes the GPU's memory later makes it before that,
+// or sets CUDA_MODULE_LOADING=EAGER so the load happens with the library's.
+// All calls share the array and it keeps the contents of the last call:
+// calls whose work overlaps on the GPU (different streams, or threads) race
+// on it.
 
 #include <cmath>
 #include <mutex>
@@ -92,8 +98,15 @@ extern "C" int gbfwi_misfit_noalloc(const float *syn, const float *obs, int nsho
 {
     if (!syn || !obs || !misfit || nshot < 1 || samples_per_shot < 1 || !(dt > 0)) return GBFWI_EINVAL;
     if (nshot > kMaxShots) return GBFWI_ESCRATCH;
+    // syn and obs must be memory of the current device (gb_is_device_ptr
+    // rejects another GPU's memory), misfit host memory
     if (!gb_is_device_ptr(syn) || !gb_is_device_ptr(obs) || gb_is_device_ptr(misfit)) return GBFWI_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
+    // the call ends with a copy into host stack memory and a stream
+    // synchronisation, neither of which a capturing stream accepts
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    GB_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return GBFWI_EINVAL;
     double *scratch = nullptr;
     GB_TRY(scratch_on_current_device(&scratch));
     double *flag = scratch + kMaxShots * kBlocksPerShot + kMaxShots;

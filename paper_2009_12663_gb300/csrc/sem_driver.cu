@@ -382,6 +382,7 @@ struct History {
 extern "C" int gbfwi_forward(gbfwi_mesh *m, const int *shot_ids, int nshot, float *seis, void *stream)
 {
     if (!m || !seis) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(seis));
     GB_TRY(check_shots(m, shot_ids, nshot));
     if (!m->have_model) return GBFWI_ENOMODEL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -423,6 +424,7 @@ extern "C" int gbfwi_misfit(gbfwi_mesh *m, const int *shot_ids, int nshot, const
                             void *stream)
 {
     if (!m || !d_obs || !misfit) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(d_obs, misfit));
     GB_TRY(check_shots(m, shot_ids, nshot));
     if (!m->have_model) return GBFWI_ENOMODEL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -663,6 +665,7 @@ extern "C" int gbfwi_adjoint_gradient(gbfwi_mesh *m, const int *shot_ids, int ns
                                       double *misfit, float *grad, int ckpt_every, void *stream)
 {
     if (!m || !d_obs || !misfit || !grad) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(d_obs, misfit, grad));
     GB_TRY(check_shots(m, shot_ids, nshot));
     if (!m->have_model) return GBFWI_ENOMODEL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -901,6 +904,7 @@ extern "C" int gbfwi_precond_diag(gbfwi_mesh *m, const int *shot_ids, int nshot,
                                   double damp, float *H, float *B0, void *stream)
 {
     if (!m || !B0 || kind < 1 || kind > 4 || !(sigma > 0) || !(damp >= 0)) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(H, B0));
     GB_TRY(check_shots(m, shot_ids, nshot));
     if (!m->have_model) return GBFWI_ENOMODEL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -976,6 +980,7 @@ extern "C" int gbfwi_precond_from_hessian(gbfwi_mesh *m, const float *H, double 
                                           void *stream)
 {
     if (!m || !H || !B0 || !(sigma > 0) || !(damp >= 0)) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(H, B0));
     cudaStream_t s = (cudaStream_t)stream;
     const long long N = (long long)m->nx * m->nz;
     GB_TRY(m->w_tmp.ensure((size_t)9 * N * sizeof(float) + 4096));

@@ -989,6 +989,7 @@ extern "C" int gbfwi_unet_layer_info(const gbfwi_unet *n, int layer, int *info)
 extern "C" int gbfwi_unet_set_params(gbfwi_unet *n, const float *params, void *stream)
 {
     if (!n || !params) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(params));
     cudaStream_t s = (cudaStream_t)stream;
     GB_CUDA(cudaMemcpyAsync(n->p32.p, params, n->nparam * sizeof(float),
                             gb_is_device_ptr(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
@@ -1004,6 +1005,7 @@ extern "C" int gbfwi_unet_set_params(gbfwi_unet *n, const float *params, void *s
 extern "C" int gbfwi_unet_get_params(const gbfwi_unet *n, float *params, void *stream)
 {
     if (!n || !params) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(params));
     cudaStream_t s = (cudaStream_t)stream;
     GB_CUDA(cudaMemcpyAsync(params, n->p32.p, n->nparam * sizeof(float),
                             gb_is_device_ptr(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
@@ -1014,6 +1016,7 @@ extern "C" int gbfwi_unet_get_params(const gbfwi_unet *n, float *params, void *s
 extern "C" int gbfwi_unet_forward(gbfwi_unet *n, const float *x, float *y, void *stream)
 {
     if (!n || !x || !y) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(x, y));
     cudaStream_t s = (cudaStream_t)stream;
     const long long P0 = npix(n, 0);
     GB_TRY(stage_input(n, x, s));
@@ -1032,6 +1035,7 @@ extern "C" int gbfwi_unet_forward(gbfwi_unet *n, const float *x, float *y, void 
 extern "C" int gbfwi_unet_gradient(gbfwi_unet *n, const float *x, const float *dy, float *grad, void *stream)
 {
     if (!n || !x || !dy || !grad) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(x, dy, grad));
     cudaStream_t s = (cudaStream_t)stream;
     const long long P0 = npix(n, 0);
     const UnetLayer &O = n->layers.back();
@@ -1059,6 +1063,7 @@ extern "C" int gbfwi_unet_train_step(gbfwi_unet *n, const float *x, const float 
                                      double *loss, void *stream)
 {
     if (!n || !x || !target || batch < 1 || !(lr > 0)) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(x, target));
     cudaStream_t s = (cudaStream_t)stream;
     const long long P0 = npix(n, 0);
     const UnetLayer &O = n->layers.back();
@@ -1121,6 +1126,7 @@ extern "C" int gbfwi_unet_features(gbfwi_mesh *m, const float *rho, const float 
                                    int height, int width, float *x, void *stream)
 {
     if (!m || !rho || !vp || !vs || !x || !(sigma_m > 0) || height < 1 || width < 1) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(rho, vp, vs, x));
     cudaStream_t s = (cudaStream_t)stream;
     const int nx = m->nx, nz = m->nz;
     const long long N = (long long)nx * nz;

@@ -80,3 +80,30 @@ def test_null_handles_rejected():
     assert L.gbfwi_bfgs_apply(None, None, 1, None, ctypes.c_double(1.0), 0, None) == -1
     assert L.gbfwi_mesh_destroy(None) == 0
     assert L.gbfwi_bfgs_destroy(None) == 0
+
+
+def test_foreign_device_pointer_is_rejected_by_the_pointer_rule(tmp_path):
+    """The rule every entry point applies to its array arguments
+    (csrc/ptrclass.h), compiled with the host C compiler and fed the pointer
+    attributes a GPU would report: device memory of another device than the
+    current one is rejected, memory of the current device is used in place,
+    managed memory is reachable from any device, host memory is staged."""
+    src = tmp_path / "ptr.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "ptrclass.h"\n'
+        "int main(void) {\n"
+        "  int cases[][4] = {\n"
+        "    {GB_MEMTYPE_DEVICE, 1, 0, GB_PTR_FOREIGN}, {GB_MEMTYPE_DEVICE, 0, 1, GB_PTR_FOREIGN},\n"
+        "    {GB_MEMTYPE_DEVICE, 3, 3, GB_PTR_LOCAL}, {GB_MEMTYPE_MANAGED, 2, 0, GB_PTR_LOCAL},\n"
+        "    {GB_MEMTYPE_HOST, 1, 0, GB_PTR_HOST}, {GB_MEMTYPE_UNREGISTERED, -2, 0, GB_PTR_HOST},\n"
+        "    {GB_MEMTYPE_DEVICE, 0, -1, GB_PTR_FOREIGN}};\n"
+        "  int bad = 0;\n"
+        "  for (unsigned i = 0; i < sizeof cases / sizeof cases[0]; ++i)\n"
+        "    if (gb_classify_pointer(cases[i][0], cases[i][1], cases[i][2]) != cases[i][3]) { printf(\"%u\\n\", i); bad = 1; }\n"
+        "  return bad;\n}\n")
+    exe = tmp_path / "ptr"
+    import subprocess
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I",
+                           os.path.join(ROOT, "paper_2009_12663_gb300", "csrc"), str(src), "-o", str(exe)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout

@@ -55,6 +55,67 @@ def test_misfit_noalloc_matches_adjoint_gradient_misfit_twice():
     assert rc == 0 and abs(out1[0] - ref_shot[0]) <= 1e-4 * ref_shot[0]
 
 
+def _call(L, syn, obs, nshot, per_shot, dt, stream=None):
+    out = np.full(nshot, -1.0)
+    rc = L.gbfwi_misfit_noalloc(ctypes.c_void_p(syn.data_ptr()), ctypes.c_void_p(obs.data_ptr()), nshot,
+                                per_shot, dt, ctypes.c_void_p(out.ctypes.data), stream)
+    return rc, out
+
+
+def test_misfit_noalloc_short_shots_after_long_ones():
+    """Every block of every shot rewrites its partial sum, also when the shot
+    has fewer samples than one grid stride (64 blocks x 256 threads), so
+    most blocks see no sample: a short call after a long one must not pick
+    up the long call's partials."""
+    L = gb.lib()
+    g = torch.Generator(device=DEV).manual_seed(11)
+    long_n, short_n, dt = 3 * 64 * 256 + 17, 1000, 1e-3
+    syn = torch.randn(4, long_n, device=DEV, generator=g)
+    obs = torch.randn(4, long_n, device=DEV, generator=g)
+    rc, out = _call(L, syn, obs, 4, long_n, dt)
+    ref = 0.5 * dt * ((syn.double() - obs.double()) ** 2).sum(1).cpu().numpy()
+    assert rc == 0 and np.allclose(out, ref, rtol=1e-12)
+    s2, o2 = syn[:, :short_n].contiguous(), obs[:, :short_n].contiguous()
+    for _ in range(2):
+        rc, out = _call(L, s2, o2, 4, short_n, dt)
+        ref = 0.5 * dt * ((s2.double() - o2.double()) ** 2).sum(1).cpu().numpy()
+        assert rc == 0 and np.allclose(out, ref, rtol=1e-12), (out, ref)
+
+
+def test_misfit_noalloc_reserves_no_device_memory():
+    """After a first call on the device (which loads the library's device
+    code and its fixed scratch array), further calls leave the device's free
+    memory unchanged."""
+    L = gb.lib()
+    syn = torch.ones(8, 5000, device=DEV)
+    obs = torch.zeros(8, 5000, device=DEV)
+    rc, _ = _call(L, syn, obs, 8, 5000, 1e-3)
+    assert rc == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        rc, out = _call(L, syn, obs, 8, 5000, 1e-3)
+        assert rc == 0 and np.allclose(out, 0.5 * 1e-3 * 5000)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_misfit_noalloc_refuses_a_capturing_stream():
+    """The call synchronises and copies to host memory, which a stream under
+    CUDA-graph capture cannot do: it returns EINVAL instead of breaking the
+    capture."""
+    L = gb.lib()
+    syn = torch.ones(2, 100, device=DEV)
+    obs = torch.zeros(2, 100, device=DEV)
+    graph = torch.cuda.CUDAGraph()
+    rcs = []
+    with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+        st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        rcs.append(_call(L, syn, obs, 2, 100, 1e-3, st)[0])
+    assert rcs == [-1]
+
+
 def test_misfit_noalloc_rejects_more_shots_than_its_scratch():
     L = gb.lib()
     a = torch.zeros(4, device=DEV)
