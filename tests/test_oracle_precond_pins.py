@@ -144,3 +144,99 @@ def test_smooth_damp_invert_median_rule():
     for c, v in enumerate((1.0, 2.0, 4.0)):
         assert np.allclose(Hs[c], v)
         assert np.allclose(B0[c], 1.0 / (v + 0.5 * v))
+
+
+def _receiver_case():
+    m = sem.Mesh(7, 5, 20.0)
+    rng = np.random.default_rng(21)
+    rec = np.stack([rng.uniform(5, 135, 5), rng.uniform(0, 95, 5)], 1)
+    st = sem.Setup(m, 4e-4, 260, rec, free_top=1, absorb=1)
+    x, z = m.coords()
+    model = (2300 + 100 * np.cos(x / 40), 2900 + 200 * np.sin(z / 30 + x / 90), 1650 + 100 * np.cos(z / 25))
+    f = m.source_vector(63.0, 41.0, 0, 1e6)
+    stf = rng.standard_normal(st.nt + 1)          # no symmetry a time shift could hide behind
+    seis = st.forward(model, f, stf)
+    return st, model, f, stf, seis
+
+
+def test_receiver_field_level_and_time_alignment_by_duality():
+    """The receiver wavefield of Eqs. 6 and 8 is the backward simulation
+    driven by the synthetics s(m0) (after Eq. A22).  The scheme's duality
+    (its adjoint is the same recurrence run backwards) fixes both its level
+    and which step each returned level belongs to: with s = P u the records
+    of the source f stf[n] and lam_n the returned receiver field,
+        dt^2 sum_{n=1}^{nt-1} stf[n] f . lam_n = dt sum_k |s_k|^2.
+    A missing dt factor, or lam shifted by one step, breaks the identity."""
+    st, model, f, stf, seis = _receiver_case()
+    lam, _ = sem.receiver_field(st, model, seis)
+    assert lam.shape[0] == st.nt + 1
+    rhs = st.dt * np.sum(seis * seis)
+    lhs = st.dt ** 2 * sum(stf[n] * np.sum(f * lam[n]) for n in range(1, st.nt))
+    assert rhs > 0 and abs(lhs - rhs) <= 1e-12 * rhs
+    for shift in (-1, 1):
+        moved = st.dt ** 2 * sum(stf[n] * np.sum(f * lam[n + shift]) for n in range(1, st.nt))
+        assert abs(moved - rhs) > 1e-2 * rhs
+
+
+def test_receiver_field_acceleration_is_the_recurrence_acceleration():
+    """P2/P4 pair the forward acceleration a_n with the receiver field's
+    acceleration at the same step n.  Where the Stacey damping is zero the
+    backward recurrence reads M (lam_{n+1} - 2 lam_n + lam_{n-1}) =
+    -dt^2 K lam_n + P^T g_n (g_n = dt s_n, its driving term), so the stored
+    acceleration at index n must equal M^-1 (-K lam_n + P^T s_n / dt),
+    built here from the oracle's stiffness, mass and receiver weights."""
+    st, model, f, stf, seis = _receiver_case()
+    lam, acc = sem.receiver_field(st, model, seis)
+    m = st.mesh
+    rho = model[0]
+    M = m.mass(rho)[..., None]
+    C = m.stacey(*model, free_top=st.free_top, absorb=st.absorb)
+    lam_, mu_ = sem.lame(*model)
+    free = C == 0.0
+    scale = np.max(np.abs(acc))
+    for n in (1, 37, 130, st.nt - 1, st.nt):
+        force = -m.stiffness(lam_, mu_, lam[n])
+        flat = force.reshape(-1, 2)
+        for r in range(st.nrec):
+            for c in range(2):
+                np.add.at(flat[:, c], st.ridx[r], st.rw[r] * seis[r, c, n - 1] / st.dt)
+        expect = force / M
+        assert np.max(np.abs(acc[n][free] - expect[free])) <= 1e-9 * scale, n
+
+
+def test_p1_homogeneous_full_space_closed_form():
+    """P1 (Eq. 5, the forward field's int a.a dt, times the node's quadrature
+    measure) for a point force in a homogeneous full space against the same
+    integral of the closed-form field: the acceleration is -omega^2 times the
+    2-D Green's tensor convolved with the Ricker wavelet (the tensor the
+    point-force pin of test_oracle_dynamics uses), summed over the same
+    samples t_1..t_nt.  Nodes 150 m from the source; the window ends before
+    the first boundary reflection reaches them.  Loose: 1%."""
+    from test_oracle_dynamics import _green_2d, _homog
+    h, ne, dt, f0, T = 20.0, 40, 4e-4, 25.0, 0.2
+    L = ne * h
+    xs = zs = L / 2
+    vp, vs, rho = 3000.0, 1732.0, 2500.0
+    t0, nt = 1.2 / f0, int(round(T / dt))
+    m = sem.Mesh(ne, ne, h)
+    st = sem.Setup(m, dt, nt, np.array([[xs, zs]]), free_top=0, absorb=1)
+    model = _homog(m, vp, vs, rho)
+    x, z = m.coords()
+    W = m.measure()
+    nfft = 1 << int(np.ceil(np.log2(6.0 / dt)))
+    omega = 2 * np.pi * np.fft.rfftfreq(nfft, dt)
+    tt = np.arange(nfft) * dt
+    arg = (np.pi * f0 * (tt - t0)) ** 2
+    F = np.fft.rfft((1 - 2 * arg) * np.exp(-arg))
+    for ftype, j in ((1, 0), (2, 1)):
+        P1 = sem.precond_raw(st, model, [dict(x=xs, z=zs, type=ftype, f0=f0, t0=t0, amp=1e9)], 1)
+        assert np.array_equal(P1[0], P1[1]) and np.array_equal(P1[0], P1[2])
+        for dx, dz in ((150.0, 0.0), (0.0, 150.0), (-110.0, 110.0), (130.0, -70.0)):
+            ix = int(np.argmin(np.abs(x[0] - (xs + dx))))
+            iz = int(np.argmin(np.abs(z[:, 0] - (zs + dz))))
+            G = np.zeros((len(omega), 2, 2), dtype=complex)
+            G[1:] = _green_2d(omega[1:], x[iz, ix] - xs, z[iz, ix] - zs, vp, vs, rho)
+            acc = [np.fft.irfft(-omega ** 2 * np.conj(G[:, i, j]) * F * 1e9, nfft)[1:nt + 1] for i in range(2)]
+            expect = dt * sum(np.sum(a * a) for a in acc)
+            got = P1[0, iz, ix] / W[iz, ix]
+            assert abs(got / expect - 1) < 1e-2, (ftype, dx, dz, got, expect)
