@@ -3,21 +3,26 @@
 
 One step = one FWI iteration's device work on the 340 x 70 element
 Marmousi-shaped model (17 km x 3.5 km, NGLL 5, 382,441 GLL points, 24
-explosive 5 Hz shots, 341 receivers, dt 0.5 ms, 12000 steps, one shot per
-launch; by default four single-shot launch streams run side by side and
-each stream replays its time loops as CUDA graphs):
+explosive 5 Hz shots, 341 receivers, dt 0.5 ms, 12000 steps):
   set_model -> adjoint_gradient (24 x (forward + adjoint + kernel)) ->
   bfgs_update -> lowrank_invhess (50-pair store, 60 probes, rank 50,
   n = 3 x 382,441).
+The launch schedule (element tile, shots per launch, concurrent launch
+streams, CUDA graphs, checkpoint interval) is the autotuner's pick for this
+mesh unless flags fix it.
 metric: GLL-point-updates/s = 2 * shots * N_glob * nt / step time; the line
-also reports s per gradient and s per rank-k UQ.  After the timed region it
-times, outside `value`, the exact low-rank decomposition of the same store
-(`uq_exact`) and the learned-preconditioner U-Net at 256 x 1024
-(`learned_preconditioner`, skipped with --no-unet).
+also reports s per gradient and s per rank-k UQ, the roofline of the
+adjoint step kernel and of the UQ.  After the timed region it times, outside
+`value`: the batched form (all 24 shots in one shot-indexed launch,
+checkpoints every 400 steps with recomputation, graph replay; `config3`),
+the exact low-rank decomposition of the same store (`uq_exact`) and the
+learned-preconditioner U-Net at 256 x 1024 (`learned_preconditioner`,
+skipped with --no-unet).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun every rank runs its own 24 shots (weak scaling); rank 0
-prints one JSON line.
+Under torchrun the 24 shots of each gradient are partitioned over the ranks
+(one sum-allreduce of the gradient and the misfit per step; strong scaling);
+rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -41,6 +46,7 @@ import synth  # noqa: E402
 METRIC = "GLL-point-updates/s fwd+adj+kernel (HBM % peak); s per FWI gradient; s per rank-k UQ"
 ADJ_BYTES_PER_POINT = 76       # adjoint step: w r/w 16, wh r/w 16, material 12, u_k 8, 3 accumulators r/w 24
 FWD_BYTES_PER_POINT = 44       # forward step: u r/w 16, vh r/w 16, material 12
+UQ_ALG_ROWS = 620              # FP32 rows of n one rank-k UQ must move at least (S, B0 Y twice, X twice, E, basis, V)
 
 
 def parse():
@@ -51,11 +57,14 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--nt", type=int, default=12000, help="time steps (12000 is the benchmark workload)")
     ap.add_argument("--shots", type=int, default=24)
-    ap.add_argument("--tile", type=int, default=None)
-    ap.add_argument("--shots-per-launch", type=int, default=1)
-    ap.add_argument("--ckpt", type=int, default=0)
-    ap.add_argument("--graph", type=int, default=1, help="1: replay the time loops as CUDA graphs")
-    ap.add_argument("--streams", type=int, default=4, help="single-shot launches simulated concurrently")
+    ap.add_argument("--tile", type=int, default=None, help="element-tile variant (default: the autotuner's)")
+    ap.add_argument("--shots-per-launch", type=int, default=None)
+    ap.add_argument("--ckpt", type=int, default=None)
+    ap.add_argument("--graph", type=int, default=None, help="1: replay the time loops as CUDA graphs")
+    ap.add_argument("--streams", type=int, default=None, help="shot batches simulated concurrently")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner: 1 shot per launch, 4 streams, graphs, tile 0, full history")
+    ap.add_argument("--no-config3", action="store_true", help="skip the batched checkpointed form")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-unet", action="store_true", help="skip the learned-preconditioner timing")
@@ -197,7 +206,7 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GLL-point-updates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name + f", {wl.nshot} shots, {wl.nrec} receivers, nt {wl.nt}",
                    "sample": f"{ns} shots x first {nt_s} steps per step (FP64 oracle, forward+adjoint+gradient)"},
@@ -268,11 +277,79 @@ def time_unet(dev, peak_tflops: float, iters: int = 5, warmup: int = 3):
             "note": "whole forward (im2col + GEMM + epilogues) over the convolution FLOPs; not part of `value`"}
 
 
+def choose_schedule(args, wl, srcs, model):
+    """The autotuner's schedule for this mesh and shot set (unless
+    --no-tune), with any schedule flag given on the command line taking
+    precedence.  Returns (schedule, tuner pick or None, tuner timings)."""
+    sch = dict(shots_per_launch=1, tile=0, use_graph=1, ckpt_every=0, streams=4)
+    tuned, timings = None, []
+    if not args.no_tune:
+        from paper_2009_12663_gb300 import autotune
+        tuned, timings = autotune.tune(wl.nex, wl.nez, wl.h, wl.dt, wl.nt, srcs, wl.rec_xz, model)
+        sch = dict(tuned)
+    for key, val in (("tile", args.tile), ("shots_per_launch", args.shots_per_launch), ("ckpt_every", args.ckpt),
+                     ("use_graph", args.graph), ("streams", args.streams)):
+        if val is not None:
+            sch[key] = int(val)
+    return sch, tuned, timings
+
+
+def adjoint_kernel_roofline(ph, sch, nshot, N, peak_gbs):
+    """Average adjoint-step launch duration from the per-phase CUDA events of
+    the last timed gradient, and the algorithmic bandwidth it sustains:
+    lanes x algorithmic bytes per launch / launch duration (`lanes` batches
+    run their identical phases side by side).  A batched launch of S shots
+    reads the material once: (64 S + 12) bytes per point."""
+    spl = min(sch["shots_per_launch"], nshot)
+    lanes = max(1, min(sch["streams"], -(-nshot // spl)))
+    ck = sch["ckpt_every"] > 0
+    adj_unit = (ADJ_BYTES_PER_POINT - 12) * N * spl + 12 * N
+    fwd_unit = (FWD_BYTES_PER_POINT - 12) * N * spl + 12 * N
+    # with checkpointing the adjoint phase also replays the forward segments
+    adj_kernel_ms = ph["adj_ms"] - (ph["fwd_ms"] if ck else 0.0)
+    n_adj = ph["adj_launches"] // (2 if ck else 1)
+    adj_us = 1e3 * adj_kernel_ms / n_adj
+    fwd_us = 1e3 * ph["fwd_ms"] / ph["fwd_launches"]
+    achieved = lanes * adj_unit / (adj_us / 1e6) / 1e9
+    fwd_achieved = lanes * fwd_unit / (fwd_us / 1e6) / 1e9
+    return dict(lanes=lanes, spl=spl, adj_unit=adj_unit, fwd_unit=fwd_unit, adj_us=adj_us, fwd_us=fwd_us,
+                achieved=achieved, frac=achieved / peak_gbs, fwd_achieved=fwd_achieved,
+                fwd_frac=fwd_achieved / peak_gbs)
+
+
+def time_config3(m, shots, d_obs, grad, tile, N, nt, peak_gbs, reps=2):
+    """The batched form: all shots in one shot-indexed launch, forward
+    snapshots every 400 steps with segment recomputation in the adjoint,
+    every pass replayed as a CUDA graph.  s per gradient from CUDA events
+    around whole gradients, adjoint-kernel roofline from the phase events."""
+    import torch
+    sch = dict(shots_per_launch=len(shots), tile=tile, use_graph=1, ckpt_every=400, streams=1)
+    m.set_schedule(**sch)
+    stream = torch.cuda.current_stream()
+    m.adjoint_gradient(shots, d_obs, grad)                  # capture
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        m.adjoint_gradient(shots, d_obs, grad)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s_grad = e0.elapsed_time(e1) / 1e3 / reps
+    r = adjoint_kernel_roofline(m.last_phase_times(), sch, len(shots), N, peak_gbs)
+    return {"schedule": sch, "s_per_gradient": s_grad,
+            "gll_point_updates_per_s": 2.0 * len(shots) * N * nt / s_grad,
+            "adjoint_kernel": {"avg_launch_us": r["adj_us"], "algorithmic_bytes_per_launch": r["adj_unit"],
+                               "achieved": r["achieved"], "frac": r["frac"]},
+            "forward_kernel": {"avg_launch_us": r["fwd_us"], "achieved": r["fwd_achieved"], "frac": r["fwd_frac"]},
+            "note": "all shots in one shot-indexed launch, checkpoint every 400 steps with recomputation "
+                    "(the adjoint phase replays each forward segment), graph replay; not part of `value`"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
 
     import paper_2009_12663_gb300 as gb
+    from paper_2009_12663_gb300.sharding import shard, sharded_adjoint_gradient
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -290,34 +367,39 @@ def run_ours(args):
 
     wl = build_problem(args)
     srcs = wl.sources(amp=1e12)
+    shots = list(range(wl.nshot))
+    mine = shard(wl.nshot, rank, world)                 # this rank's shots (all of them at N = 1)
     m = gb.Mesh(wl.nex, wl.nez, wl.h, wl.dt, wl.nt, srcs, wl.rec_xz, free_surface_top=1)
-    tile = args.tile if args.tile is not None else 0
-    m.set_schedule(shots_per_launch=args.shots_per_launch, tile=tile, use_graph=args.graph, ckpt_every=args.ckpt,
-                   streams=args.streams)
     x, z = m.node_coords()
     W, H = wl.nex * wl.h, wl.nez * wl.h
-    seed = 2024 + rank
+    seed = 2024
     true = [torch.tensor(a, dtype=torch.float32, device=dev) for a in synth.marmousi_like(x, z, seed, W, H)]
     start = [torch.tensor(a, dtype=torch.float32, device=dev) for a in synth.marmousi_like_smooth(x, z, seed, W, H)]
-    shots = list(range(wl.nshot))
     N = m.nglob
     n = 3 * N
+    sch, tuned, tune_timings = choose_schedule(args, wl, [srcs[i] for i in mine], start)
+    m.set_schedule(**sch)
 
-    # observed data from the true model (untimed)
+    # observed data of this rank's shots from the true model (untimed)
     m.set_model(*true)
-    d_obs = torch.zeros(wl.nshot, wl.nrec, 2, wl.nt, device=dev)
-    m.forward(shots, d_obs)
+    d_obs = torch.zeros(len(mine), wl.nrec, 2, wl.nt, device=dev)
+    m.forward([shots[i] for i in mine], d_obs)
     grad = torch.zeros(3, m.nz, m.nx, device=dev)
+
+    def gradient(model_d_obs, g):
+        if world > 1:
+            return sharded_adjoint_gradient(m, shots, model_d_obs, g)
+        return m.adjoint_gradient(shots, model_d_obs, g)
 
     # BFGS stores: UQ store with 50 pairs (synthetic history at full n), and
     # an iteration store receiving one pair per step
-    S, Y, B0 = synth.synthetic_history(77 + rank, n, 50)
+    S, Y, B0 = synth.synthetic_history(77, n, 50)
     B0d = torch.tensor(B0, device=dev)
     uq = gb.Bfgs(n, 50, B0d)
     for i in range(50):
         uq.update(torch.tensor(S[i], device=dev), torch.tensor(Y[i], device=dev))
     total_steps = args.warmup + args.steps + (0 if args.no_e2e else args.steps)
-    S2, Y2, _ = synth.synthetic_history(99 + rank, n, total_steps)
+    S2, Y2, _ = synth.synthetic_history(99, n, total_steps)
     S2d, Y2d = torch.tensor(S2, device=dev), torch.tensor(Y2, device=dev)
     it = gb.Bfgs(n, total_steps, B0d)
     p, rnk = 60, 50
@@ -334,19 +416,20 @@ def run_ours(args):
         if timers:
             timers[0].record(stream)
         m.set_model(*start)
-        m.adjoint_gradient(shots, d_obs, grad)
+        gradient(d_obs, grad)
         if timers:
             timers[1].record(stream)
         it.update(S2d[i], Y2d[i])
-        uq.lowrank_invhess(p, rnk, seed=1000 + i, eps_prior=1.0, V=V, lam=lam, std=std)
         if timers:
             timers[2].record(stream)
+        uq.lowrank_invhess(p, rnk, seed=1000 + i, eps_prior=1.0, V=V, lam=lam, std=std)
+        if timers:
+            timers[3].record(stream)
 
     for _ in range(args.warmup):
         step()
     clocks = Clocks(dev.index)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    phase = []
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     barrier()
     l0 = gb.launch_count()
     clocks.start()
@@ -355,7 +438,6 @@ def run_ours(args):
     t0.record(stream)
     for k in range(args.steps):
         step(ev[k])
-        phase.append(None)
     t1.record(stream)
     barrier()
     ck = clocks.stop()
@@ -363,13 +445,13 @@ def run_ours(args):
     ph = m.last_phase_times()
     ms = t0.elapsed_time(t1) / args.steps
     grad_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
-    uq_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    uq_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in ev]))
     if world > 1:
         tt = torch.tensor([ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
-    updates_per_step = 2.0 * wl.nshot * N * wl.nt
-    value = world * updates_per_step / (ms / 1e3)
+    updates_per_step = 2.0 * wl.nshot * N * wl.nt          # the whole job: every rank's shots
+    value = updates_per_step / (ms / 1e3)
 
     # end to end through host buffers (pinned), copies inside the timed region
     e2e = None
@@ -386,7 +468,7 @@ def run_ours(args):
             i = step_i[0]
             step_i[0] += 1
             m.set_model(*h_model)
-            m.adjoint_gradient(shots, h_obs, h_grad)
+            gradient(h_obs, h_grad)
             it.update(h_s[i], h_y[i])
             uq.lowrank_invhess(p, rnk, seed=1000 + i, eps_prior=1.0, std=h_std)
         barrier()
@@ -397,7 +479,7 @@ def run_ours(args):
             e2e_s = float(tt.item())
         h2d = 3 * N * 4 + h_obs.numel() * 4 + 2 * n * 4
         d2h = 3 * N * 4 + n * 4 + 8
-        e2e = {"value": world * updates_per_step / e2e_s, "unit": "GLL-point-updates/s",
+        e2e = {"value": updates_per_step / e2e_s, "unit": "GLL-point-updates/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s}
 
     if rank != 0:
@@ -406,33 +488,35 @@ def run_ours(args):
         return 0
 
     pk, pk_kind = peaks()
-    spl = m.schedule["shots_per_launch"]
-    lanes = max(1, min(m.schedule["streams"], (wl.nshot + spl - 1) // spl))
-    tx, tz = gb.tile_shape(m.schedule["tile"])
-    adj_unit = ADJ_BYTES_PER_POINT * N * spl          # algorithmic bytes per adjoint launch
-    fwd_unit = FWD_BYTES_PER_POINT * N * spl
-    # with checkpointing the adjoint phase also replays the forward segments
-    adj_kernel_ms = ph["adj_ms"] - (ph["fwd_ms"] if args.ckpt else 0.0)
-    n_adj = ph["adj_launches"] // (2 if args.ckpt else 1)
-    adj_us = 1e3 * adj_kernel_ms / n_adj
-    fwd_us = 1e3 * ph["fwd_ms"] / ph["fwd_launches"]
-    # `lanes` single-shot streams run their (identical) phases side by side, so the
-    # bandwidth the kernel sustains is lanes x bytes per launch / launch duration
-    achieved = lanes * adj_unit / (adj_us / 1e6) / 1e9
-    fwd_achieved = lanes * fwd_unit / (fwd_us / 1e6) / 1e9
-    step_bytes = (ADJ_BYTES_PER_POINT + FWD_BYTES_PER_POINT) * N * wl.nshot * wl.nt
-    tr = traffic_record(f"adjoint_step_{tx}x{tz}_spl{spl}")
-    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": (tr or {}).get("bytes_per_launch"),
+    r = adjoint_kernel_roofline(ph, sch, len(mine), N, pk["hbm_gbs"])
+    tx, tz = gb.tile_shape(sch["tile"])
+    step_bytes = (ADJ_BYTES_PER_POINT + FWD_BYTES_PER_POINT) * N * len(mine) * wl.nt
+    tr = traffic_record(f"adjoint_step_{tx}x{tz}_spl{r['spl']}_lanes{r['lanes']}")
+    roof = {"bound": "hbm", "achieved": r["achieved"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": r["frac"], "traffic": (tr or {}).get("bytes_per_launch"),
             "kernel": f"sem_step_kernel<{tx},{tz},ADJ_G> (adjoint step + gradient correlation)",
-            "algorithmic_bytes_per_launch": adj_unit, "avg_launch_us": adj_us, "concurrent_lanes": lanes,
-            "peak_kind": pk_kind,
+            "algorithmic_bytes_per_launch": r["adj_unit"], "avg_launch_us": r["adj_us"],
+            "concurrent_lanes": r["lanes"], "peak_kind": pk_kind,
+            "meaning": "algorithmic bytes (76 B per point and shot: fields, material, history, accumulators) "
+                       "over the CUDA-event launch duration, i.e. effective bandwidth; a lane's per-step "
+                       "working set (~17 MB) stays in L2, so DRAM moves less (traffic)",
             "timing": "CUDA events on each launching stream around every adjoint pass",
             "whole_gradient": {"algorithmic_bytes": step_bytes,
                                "achieved": step_bytes / (grad_ms / 1e3) / 1e9,
                                "frac": step_bytes / (grad_ms / 1e3) / 1e9 / pk["hbm_gbs"]},
-            "forward_kernel": {"achieved": fwd_achieved, "frac": fwd_achieved / pk["hbm_gbs"],
-                               "algorithmic_bytes_per_launch": fwd_unit, "avg_launch_us": fwd_us}}
+            "forward_kernel": {"achieved": r["fwd_achieved"], "frac": r["fwd_frac"],
+                               "algorithmic_bytes_per_launch": r["fwd_unit"], "avg_launch_us": r["fwd_us"]}}
+    uq_bytes = UQ_ALG_ROWS * n * 4
+    roof_uq = {"bound": "hbm", "achieved": uq_bytes / (uq_ms / 1e3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+               "frac": uq_bytes / (uq_ms / 1e3) / 1e9 / pk["hbm_gbs"], "algorithmic_bytes": uq_bytes,
+               "s_per_uq": uq_ms / 1e3, "peak_kind": pk_kind,
+               "definition": f"{UQ_ALG_ROWS} FP32 rows of n: two passes over S and B0 Y (200), X read twice "
+                             "and E written (180), the basis and V passes (4 x 60)",
+               "timing": "CUDA events around gbfwi_lowrank_invhess"}
+
+    c3 = None
+    if not args.no_config3 and world == 1:
+        c3 = time_config3(m, shots, d_obs, grad, sch["tile"], N, wl.nt, pk["hbm_gbs"])
 
     # exact low-rank decomposition of the same 50-pair store (no probes),
     # timed after the timed region
@@ -462,17 +546,22 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "GLL-point-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{wl.name}, {wl.nshot} shots x {wl.nt} steps, {wl.nrec} receivers, "
-                               f"{spl} shot(s) per launch, {lanes} concurrent launch streams, "
-                               f"CUDA graphs {'on' if args.graph else 'off'}; UQ n={n}, k=50 pairs, p={p}, rank {rnk}",
-                   "nglob": N, "nt": wl.nt, "shots": wl.nshot, "tile": m.schedule,
-                   "l2": "inputs larger than L2 (36.7 GB forward history per shot)"},
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{wl.name}, {wl.nshot} shots x {wl.nt} steps, {wl.nrec} receivers; "
+                               f"UQ n={n}, k=50 pairs, p={p}, rank {rnk}",
+                   "nglob": N, "nt": wl.nt, "shots": wl.nshot, "shots_per_rank": len(mine),
+                   "schedule": sch, "schedule_source": "autotuner" if tuned is not None else "fixed",
+                   "autotuner_pick": tuned, "autotuner_probes": len(tune_timings),
+                   "parallelism": f"shots partitioned over {world} rank(s), one gradient allreduce per step",
+                   "l2": "each step streams the forward history (36.7 GB per shot, larger than L2) through HBM; "
+                         "a lane's per-step working set (~17 MB) stays L2-resident"},
         "s_per_gradient": grad_ms / 1e3, "s_per_uq": uq_ms / 1e3,
         "gpu_launches": launches,
         "roofline": roof,
+        "roofline_uq": roof_uq,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "config3": c3,
         "uq_exact": uq_exact,
         "learned_preconditioner": unet,
         "clocks": ck,

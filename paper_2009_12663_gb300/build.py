@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUTDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUTDIR, "libgbfwi.so")
-SOURCES = ["mesh.cu", "sem_step.cu", "sem_driver.cu", "bfgs.cu", "misfit_noalloc.cu", "unet.cu"]
+SOURCES = ["mesh.cu", "sem_step.cu", "sem_driver.cu", "bfgs.cu", "tc_products.cu", "misfit_noalloc.cu", "unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

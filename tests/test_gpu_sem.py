@@ -181,8 +181,19 @@ def test_autotuner_returns_a_valid_schedule(c2):
     wl = c2.wl
     model = [t32(a) for a in c2.start]
     best, timings = autotune.tune(wl.nex, wl.nez, wl.h, wl.dt, wl.nt, c2.srcs, wl.rec_xz, model,
-                                  spl_options=(1, 2), tiles=(0, 2), probe_nt=40, use_cache=False)
-    assert len(timings) == 8
+                                  spl_options=(1, 2), stream_options=(1, 2), ckpt_options=(100,), tiles=(0, 2),
+                                  probe_nt=40, repeats=2, use_cache=False)
+    scheds = [t["schedule"] for t in timings]
+    # every axis of the schedule is searched: tile, shots per launch, lanes,
+    # checkpoint interval, graphs
+    assert {s["tile"] for s in scheds} == {0, 2}
+    assert {s["shots_per_launch"] for s in scheds} == {1, 2}
+    assert {s["streams"] for s in scheds} == {1, 2}
+    assert {s["ckpt_every"] for s in scheds} == {0, 100}
+    assert {s["use_graph"] for s in scheds} == {0, 1}
+    assert best in scheds
+    assert min(t["us_per_shot_step"] for t in timings) == next(t["us_per_shot_step"] for t in timings
+                                                                if t["schedule"] == best)
     m = c2.mesh(**best)
     f, g = c2.gpu_gradient(m, [0, 1], obs=c2.obs_gpu)
     ref = c2.gpu_gradient(c2.mesh(), [0, 1], obs=c2.obs_gpu)

@@ -61,3 +61,48 @@ def test_two_rank_gloo_gradient_equals_single_process():
         res = np.load(out)
     assert abs(res[0] - f) <= 1e-12 * f
     assert np.allclose(res[1:].reshape(g.shape), g, rtol=1e-12, atol=1e-12 * np.abs(g).max())
+
+
+def _rank_product(rank, world, path, out, nshot):
+    """One rank of sharded_adjoint_gradient, the product's partition and
+    reduction, with the oracle standing in for the per-rank CUDA compute."""
+    from oracle import sem
+    from paper_2009_12663_gb300.sharding import sharded_adjoint_gradient
+    dist.init_process_group("gloo", init_method=f"file://{path}", rank=rank, world_size=world)
+    st, start, srcs, obs = _case()
+    srcs, obs = srcs[:nshot], obs[:nshot]
+    ids = list(range(len(srcs)))
+    calls = []
+
+    def stand_in(my_ids, d_blk, g):
+        calls.append(list(my_ids))
+        f, gr, _ = sem.misfit_gradient(st, start, [srcs[i] for i in my_ids], list(d_blk))
+        g.copy_(torch.tensor(gr))
+        return f
+
+    grad = torch.full((3, st.mesh.nz, st.mesh.nx), float("nan"), dtype=torch.float64)
+    total = sharded_adjoint_gradient(None, ids, np.stack(obs), grad, compute=stand_in)
+    np.save(out + f".{rank}.npy", np.concatenate([[total], grad.numpy().ravel()]))
+    with open(out + f".{rank}.calls", "w") as fh:
+        fh.write(repr(calls))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,nshot", [(2, 4), (3, 2)])
+def test_sharded_adjoint_gradient_equals_single_process(world, nshot):
+    """Every rank ends with the single-process misfit and gradient; each
+    rank computed only its own block of shots (a rank without shots adds
+    zeros)."""
+    from oracle import sem
+    st, start, srcs, obs = _case()
+    f, g, _ = sem.misfit_gradient(st, start, srcs[:nshot], obs[:nshot])
+    with tempfile.TemporaryDirectory() as d:
+        out = os.path.join(d, "res")
+        mp.spawn(_rank_product, args=(world, os.path.join(d, "pg"), out, nshot), nprocs=world, join=True)
+        for r in range(world):
+            res = np.load(out + f".{r}.npy")
+            calls = eval(open(out + f".{r}.calls").read())
+            mine = shard(nshot, r, world)
+            assert calls == ([mine] if mine else [])
+            assert abs(res[0] - f) <= 1e-12 * f
+            assert np.allclose(res[1:].reshape(g.shape), g, rtol=1e-12, atol=1e-12 * np.abs(g).max())
