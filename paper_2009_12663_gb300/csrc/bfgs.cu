@@ -9,13 +9,16 @@
 // with R_ij = s_i^T y_j (i <= j), D = diag(s_i^T y_i).  It equals the
 // recursion of Eq. 3 and the two-loop recursions of Algorithms 1-2.
 //
-// Layout: vectors are rows, S / Y / B0Y are [kmax][n] FP32, blocks X / E / Q /
-// V are [p][n] FP32.  The n-long work is (a) split-K products A B^T with a
-// deterministic FP64 reduction over the splits (FP32 or compensated sums
-// within a split) and (b) row combinations out = coef * rows; the small
-// matrices (middle matrix, pivoted and plain Cholesky factors, the solve
-// for Omega) are FP64 in one CTA, and the small symmetric eigenproblems run
-// as FP32 block Jacobi sweeps in one CTA.
+// Layout: vectors are rows, S / Y / B0Y are [kmax][ld] FP32, blocks X / E / Q /
+// V are [p][ld] FP32, with the row pitch ld = n rounded up to 64 floats so
+// that every row starts on a 256-byte boundary.  The n-long work is (a)
+// split-K products A B^T on the tensor cores (3xTF32, compensated sums
+// within a split, a deterministic FP64 reduction over the splits;
+// tc_products.cu), or compensated CUDA-core dot products for one or two
+// columns, and (b) row combinations out = coef * rows on the tensor cores;
+// the small matrices (middle matrix, pivoted and plain Cholesky factors,
+// the solve for Omega) are FP64 in one CTA, and the small symmetric
+// eigenproblems run as FP32 block Jacobi sweeps in one CTA.
 //
 // The low-rank part (Algorithm 3, gbfwi_lowrank_invhess): E = (B - B0) X,
 // a rank-revealing orthonormal basis Q of E (pivoted Cholesky of E E^T,
@@ -31,6 +34,7 @@
 
 struct gbfwi_bfgs {
     long long n = 0;
+    long long ld = 0;          // row pitch of every [rows][n] block: n rounded up to 64
     int kmax = 0, k = 0;
     DevBuf S, Y, BY, B0;       // [kmax][n] x 3, [n]
     std::vector<double> SY;    // [kmax][kmax]: SY[i*kmax + j] = s_i^T y_j (i <= j)
@@ -46,9 +50,6 @@ struct gbfwi_bfgs {
 };
 
 namespace {
-
-constexpr int AT = 64;          // output tile of the split-K product
-constexpr int KI = 32;          // i-chunk staged per step
 
 // One term of a compensated FP32 dot product (Ogita, Rump & Oishi 2005,
 // "Accurate sum and dot product", algorithm Dot2): the product is split
@@ -68,91 +69,10 @@ __device__ __forceinline__ void dot2_term(float a, float b, float &hi, float &lo
     lo = __fadd_rn(lo, __fadd_rn(se, pe));
 }
 
-// part[sx][a][b] = sum_{i in split sx} A[a][i] * w[i] * Bm[b][i]
-// Tiles of 64 rows x 32 columns of A and Bm are staged through two shared
-// buffers; the global loads of the next tile are issued before the current
-// tile is consumed.  ACC2 = false: plain FP32 accumulation within a split
-// (relative error ~1e-6, enough for the search direction); ACC2 = true:
-// compensated (Dot2) accumulation, for Gram matrices and projections of
-// ill-conditioned blocks in the randomized SVD.
-template <bool ACC2>
-__global__ void __launch_bounds__(256) atb_partial(const float *__restrict__ A, long long lda, int ka,
-                                                   const float *__restrict__ Bm, long long ldb, int kb,
-                                                   const float *__restrict__ w, long long n, long long chunk,
-                                                   double *__restrict__ part)
-{
-    __shared__ float As[2][KI][AT + 1];
-    __shared__ float Bs[2][KI][AT + 1];
-    const int sx = blockIdx.x, a0 = blockIdx.y * AT, b0 = blockIdx.z * AT;
-    const long long ib = (long long)sx * chunk, ie = min(n, ib + chunk);
-    const int t = threadIdx.x, ty = t / 16, tx = t % 16;
-    constexpr int PER = AT * KI / 256;      // elements per thread per tile (8)
-    float ra[PER], rb[PER];
-    auto fetch = [&](long long i0) {
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            int q = t + u * 256;
-            int r = q / KI, ii = q - r * KI;
-            long long i = i0 + ii;
-            bool ok = i < ie;
-            ra[u] = (ok && a0 + r < ka) ? __ldg(A + (long long)(a0 + r) * lda + i) : 0.f;
-            float bv = (ok && b0 + r < kb) ? __ldg(Bm + (long long)(b0 + r) * ldb + i) : 0.f;
-            if (w && ok) bv *= __ldg(w + i);
-            rb[u] = bv;
-        }
-    };
-    auto stash = [&](int buf) {
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            int q = t + u * 256;
-            int r = q / KI, ii = q - r * KI;
-            As[buf][ii][r] = ra[u];
-            Bs[buf][ii][r] = rb[u];
-        }
-    };
-    float acc[4][4] = {};
-    float lo[4][4] = {};
-    int buf = 0;
-    if (ib < ie) {
-        fetch(ib);
-        stash(0);
-    }
-    __syncthreads();
-    for (long long i0 = ib; i0 < ie; i0 += KI) {
-        const bool more = i0 + KI < ie;
-        if (more) fetch(i0 + KI);
-#pragma unroll 8
-        for (int ii = 0; ii < KI; ++ii) {
-            float av[4], bv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) { av[u] = As[buf][ii][ty * 4 + u]; bv[u] = Bs[buf][ii][tx * 4 + u]; }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    if constexpr (ACC2)
-                        dot2_term(av[u], bv[v], acc[u][v], lo[u][v]);
-                    else
-                        acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
-                }
-        }
-        if (more) stash(buf ^ 1);
-        __syncthreads();
-        buf ^= 1;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            int a = a0 + ty * 4 + u, b = b0 + tx * 4 + v;
-            if (a < ka && b < kb) part[((long long)sx * ka + a) * kb + b] = (double)acc[u][v] + (double)lo[u][v];
-        }
-}
-
-// Thin form of atb_partial for kb <= 2 columns (dot products of the pair
-// updates, the search direction): CTA (split, a) accumulates row a against
-// the kb columns with compensated (Dot2) sums, then an FP64 tree over its
-// threads; same partial layout as atb_partial.
+// Products with kb <= 2 columns (dot products of the pair updates, the
+// search direction): CTA (split, a) accumulates row a against the kb
+// columns with compensated (Dot2) sums, then an FP64 tree over its threads;
+// part[sx][a][b] is reduced over the splits by atb_reduce.
 template <int KB>
 __global__ void __launch_bounds__(256) atb_thin(const float *__restrict__ A, long long lda,
                                                 const float *__restrict__ Bm, long long ldb,
@@ -310,16 +230,26 @@ __global__ void middle_kernel(const double *__restrict__ T, const double *__rest
     }
 }
 
-// Cholesky G + shift tr(G) I = R^T R (R upper, p x p, FP64, in global
-// scratch), then coef = R^-T (lower) as FP32 for the row combination
-// Q = R^-T E (one CholeskyQR pass; the first pass of shifted CholeskyQR3
-// passes shift > 0).
-__global__ void chol_kernel(const double *__restrict__ G, int p, double shift, double *__restrict__ A,
-                            double *__restrict__ R, double *__restrict__ Rinv, float *__restrict__ coef,
-                            int *__restrict__ flag)
+// Cholesky G + shift tr(G) I = R^T R (R upper, p x p), then coef = R^-T
+// (lower) for the row combination Q = R^-T E (one CholeskyQR pass; the
+// first pass of shifted CholeskyQR3 passes shift > 0).  FP32 arithmetic
+// (GB300 runs FP64 at 1/64 of the FP32 rate): a pass only needs an
+// invertible triangular R that makes the rows nearly orthonormal, since
+// R^-T E spans the rows of E for any invertible R, and the next pass
+// removes what is left; the shift (1e-5 of the trace) keeps the FP32 Gram
+// matrix definite.  The factor and its inverse live in shared memory when
+// 2 p^2 floats fit (use_smem), else in the global scratch A, Rinv.
+__global__ void chol_kernel(const double *__restrict__ G, int p, double shift, float *A, float *Rinv,
+                            float *__restrict__ coef, int *__restrict__ flag, int use_smem)
 {
+    extern __shared__ float chol_smem[];
+    if (use_smem) {
+        A = chol_smem;
+        Rinv = chol_smem + (size_t)p * p;
+    }
     const int t = threadIdx.x, nt = blockDim.x;
     __shared__ double trace;
+    __shared__ float piv;
     if (t == 0) {
         double tr = 0.0;
         for (int i = 0; i < p; ++i) tr += G[(long long)i * p + i];
@@ -327,65 +257,83 @@ __global__ void chol_kernel(const double *__restrict__ G, int p, double shift, d
     }
     __syncthreads();
     for (int q = t; q < p * p; q += nt) {
-        int i = q / p, j = q % p;
-        A[q] = G[q] + (i == j ? shift * trace : 0.0);
-        R[q] = 0.0;
+        const int i = q / p, j = q - i * p;
+        A[q] = (float)(G[q] + (i == j ? shift * trace : 0.0));
     }
     __syncthreads();
-    __shared__ double piv;
+    // right-looking factorisation in place: row j of the upper triangle
+    // becomes row j of R
     for (int j = 0; j < p; ++j) {
         if (t == 0) {
-            double dj = A[(long long)j * p + j];
-            if (!(dj > 0.0) || !isfinite(dj)) { *flag = 2; dj = 1.0; }
-            piv = sqrt(dj);
-            R[(long long)j * p + j] = piv;
+            float dj = A[(long long)j * p + j];
+            if (!(dj > 0.f) || !isfinite(dj)) { *flag = 2; dj = 1.f; }
+            piv = sqrtf(dj);
+            A[(long long)j * p + j] = piv;
         }
         __syncthreads();
-        for (int i = j + 1 + t; i < p; i += nt) R[(long long)j * p + i] = A[(long long)j * p + i] / piv;
+        const float inv = 1.f / piv;
+        for (int i = j + 1 + t; i < p; i += nt) A[(long long)j * p + i] *= inv;
         __syncthreads();
-        int m = p - j - 1;
+        const int m = p - j - 1;
         for (int q = t; q < m * m; q += nt) {
-            int r = j + 1 + q / m, c = j + 1 + q % m;
-            if (c >= r) A[(long long)r * p + c] -= R[(long long)j * p + r] * R[(long long)j * p + c];
+            const int r = j + 1 + q / m, c = j + 1 + q % m;
+            if (c >= r) A[(long long)r * p + c] = fmaf(-A[(long long)j * p + r], A[(long long)j * p + c], A[(long long)r * p + c]);
         }
         __syncthreads();
     }
-    // R^-1 by back substitution, one column per thread
+    // R^-1 (upper) by back substitution, one column per thread; the
+    // reciprocals of the diagonal go to the (unused) strict lower triangle's
+    // first column (row 0's goes to a shared word)
+    __shared__ float d0inv;
+    for (int i = t; i < p; i += nt)
+        if (i > 0) A[(long long)i * p] = 1.f / A[(long long)i * p + i];
+    if (t == 0) d0inv = 1.f / A[0];
+    __syncthreads();
     for (int c = t; c < p; c += nt) {
-        for (int i = p - 1; i >= 0; --i) {
-            double s = (i == c) ? 1.0 : 0.0;
-            for (int j = i + 1; j < p; ++j) s -= R[(long long)i * p + j] * Rinv[(long long)j * p + c];
-            Rinv[(long long)i * p + c] = s / R[(long long)i * p + i];
+        for (int i = c; i >= 0; --i) {
+            float s = (i == c) ? 1.f : 0.f;
+            for (int j = i + 1; j <= c; ++j) s = fmaf(-A[(long long)i * p + j], Rinv[(long long)j * p + c], s);
+            Rinv[(long long)i * p + c] = s * (i == 0 ? d0inv : A[(long long)i * p]);
         }
     }
     __syncthreads();
     for (int q = t; q < p * p; q += nt) {
-        int a = q / p, b = q % p;
-        coef[q] = (float)Rinv[(long long)b * p + a];   // (R^-T)[a][b]
+        const int a = q / p, b = q - a * p;
+        coef[q] = b <= a ? Rinv[(long long)b * p + a] : 0.f;   // (R^-T)[a][b]
     }
 }
 
 // Block-cooperative cyclic Jacobi for a symmetric p x p matrix A (row-major,
 // overwritten by its eigenvalues on the diagonal); U accumulates the
 // eigenvectors as columns (must hold I on entry).  Round-robin pairing gives
-// p/2 disjoint rotations per round.  A pair is rotated only while
-// |a_pq| > 1e-15 sqrt(|a_pp a_qq|) (the relative threshold of Demmel &
+// P/2 disjoint rotations per round (P = p rounded up to even); the pairing
+// of every round is tabulated once, and each thread keeps the same
+// (pair, column) items in every round.  A pair is rotated only while
+// |a_pq| > rel_eps sqrt(|a_pp a_qq|) (the relative threshold of Demmel &
 // Veselic 1992, which also resolves small eigenvalues of a graded matrix)
-// and |a_pq| > eps |A|_F (below that an entry is rounding noise of the
-// largest eigenvalues), with eps 1e-15 / 1e-16 in FP64 and 1e-7 / 1e-7 in
-// FP32; the sweeps stop after one without a rotation, or after max_sweeps.
-// cs: scratch of >= p + 1 elements.
+// and |a_pq| > abs_eps |A|_F (below that an entry is rounding noise of the
+// largest eigenvalues: rotating it changes nothing at this precision), with
+// (rel_eps, abs_eps) = (1e-15, 1e-16) in FP64 and (1e-7, 4e-7) in FP32; the
+// sweeps stop after one without a rotation, or after max_sweeps.
+// work: >= 2 P floats of rotations + P (P - 1) shorts of pairing (shared).
 template <typename T>
-__device__ void block_jacobi(T *A, T *U, int p, T *cs, int max_sweeps)
+__device__ void block_jacobi(T *A, T *U, int p, T *cs, short *pairs, int max_sweeps)
 {
     const int t = threadIdx.x, nt = blockDim.x;
     constexpr T rel_eps = sizeof(T) == 8 ? (T)1e-15 : (T)1e-7;
-    constexpr T abs_eps = sizeof(T) == 8 ? (T)1e-16 : (T)1e-7;
+    constexpr T abs_eps = sizeof(T) == 8 ? (T)1e-16 : (T)4e-7;
     __shared__ int rotated;
     __shared__ T fro;
     const int P = (p + 1) & ~1;
     const int npair = P / 2;
-    __syncthreads();
+    // pairs[round][m] = (a, b), a < b, round-robin with element 0 fixed
+    for (int q = t; q < (P - 1) * npair; q += nt) {
+        const int round = q / npair, m = q - round * npair;
+        const int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
+        const int b = 1 + (P - 2 - m + round) % (P - 1);
+        pairs[2 * q] = (short)min(a, b);
+        pairs[2 * q + 1] = (short)max(a, b);
+    }
     if (t == 0) fro = 0;
     __syncthreads();
     {
@@ -395,22 +343,23 @@ __device__ void block_jacobi(T *A, T *U, int p, T *cs, int max_sweeps)
     }
     __syncthreads();
     const T abs_tol = abs_eps * sqrt(fro);
+    const int items = npair * p;                // (pair, column) items of one update
+    // this thread's items q = t + i nt, as (pair m, column l), stepped without division
+    const int m0 = t / p, l0 = t - (t / p) * p, dm = nt / p, dl = nt - (nt / p) * p;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        __syncthreads();
         if (t == 0) rotated = 0;
         __syncthreads();
         for (int round = 0; round < P - 1; ++round) {
+            const short *pr = pairs + 2 * round * npair;
             for (int m = t; m < npair; m += nt) {
-                int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
-                int b = 1 + (P - 2 - m + round) % (P - 1);
+                const int pp = pr[2 * m], qq = pr[2 * m + 1];
                 T c = 1, sn = 0;
-                if (a < p && b < p) {
-                    int pp = min(a, b), qq = max(a, b);
-                    T apq = A[(long long)pp * p + qq];
-                    T app = A[(long long)pp * p + pp], aqq = A[(long long)qq * p + qq];
+                if (qq < p) {
+                    const T apq = A[pp * p + qq];
+                    const T app = A[pp * p + pp], aqq = A[qq * p + qq];
                     if (fabs(apq) > rel_eps * sqrt(fabs(app * aqq)) && fabs(apq) > abs_tol) {
-                        T tau = (aqq - app) / (2 * apq);
-                        T tt = (tau >= 0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
+                        const T tau = (aqq - app) / (2 * apq);
+                        const T tt = (tau >= 0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
                         c = (T)1 / sqrt((T)1 + tt * tt);
                         sn = tt * c;
                         rotated = 1;
@@ -420,35 +369,34 @@ __device__ void block_jacobi(T *A, T *U, int p, T *cs, int max_sweeps)
                 cs[2 * m + 1] = sn;
             }
             __syncthreads();
-            for (int q = t; q < npair * p; q += nt) {          // rows: A <- J^T A
-                int m = q / p, l = q % p;
-                int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
-                int b = 1 + (P - 2 - m + round) % (P - 1);
-                if (a >= p || b >= p || cs[2 * m + 1] == 0) continue;
-                int pp = min(a, b), qq = max(a, b);
-                T c = cs[2 * m], sn = cs[2 * m + 1];
-                T x = A[(long long)pp * p + l], y = A[(long long)qq * p + l];
-                A[(long long)pp * p + l] = c * x - sn * y;
-                A[(long long)qq * p + l] = sn * x + c * y;
+            for (int q = t, m = m0, l = l0; q < items; q += nt, m += dm, l += dl) {   // rows: A <- J^T A
+                if (l >= p) { l -= p; ++m; }
+                const T sn = cs[2 * m + 1];
+                if (sn == 0) continue;
+                const int pp = pr[2 * m], qq = pr[2 * m + 1];
+                const T c = cs[2 * m];
+                const T x = A[pp * p + l], y = A[qq * p + l];
+                A[pp * p + l] = c * x - sn * y;
+                A[qq * p + l] = sn * x + c * y;
             }
             __syncthreads();
-            for (int q = t; q < npair * p; q += nt) {          // columns: A <- A J, U <- U J
-                int m = q / p, l = q % p;
-                int a = m == 0 ? 0 : 1 + (m - 1 + round) % (P - 1);
-                int b = 1 + (P - 2 - m + round) % (P - 1);
-                if (a >= p || b >= p || cs[2 * m + 1] == 0) continue;
-                int pp = min(a, b), qq = max(a, b);
-                T c = cs[2 * m], sn = cs[2 * m + 1];
-                T x = A[(long long)l * p + pp], y = A[(long long)l * p + qq];
-                A[(long long)l * p + pp] = c * x - sn * y;
-                A[(long long)l * p + qq] = sn * x + c * y;
-                T u = U[(long long)l * p + pp], v = U[(long long)l * p + qq];
-                U[(long long)l * p + pp] = c * u - sn * v;
-                U[(long long)l * p + qq] = sn * u + c * v;
+            for (int q = t, m = m0, l = l0; q < items; q += nt, m += dm, l += dl) {   // columns: A <- A J, U <- U J
+                if (l >= p) { l -= p; ++m; }
+                const T sn = cs[2 * m + 1];
+                if (sn == 0) continue;
+                const int pp = pr[2 * m], qq = pr[2 * m + 1];
+                const T c = cs[2 * m];
+                const T x = A[l * p + pp], y = A[l * p + qq];
+                A[l * p + pp] = c * x - sn * y;
+                A[l * p + qq] = sn * x + c * y;
+                const T u = U[l * p + pp], v = U[l * p + qq];
+                U[l * p + pp] = c * u - sn * v;
+                U[l * p + qq] = sn * u + c * v;
             }
             __syncthreads();
         }
         if (!rotated) break;
+        __syncthreads();
     }
     __syncthreads();
 }
@@ -483,39 +431,54 @@ __global__ void gram_pivchol_kernel(const double *__restrict__ G, int p, double 
     if (t == 0) s_r = p;
     __syncthreads();
     for (int j = 0; j < p; ++j) {
-        if (t == 0) {
+        if (t < 32) {
+            // largest remaining residual (first index among equals), warp 0
             int best = -1;
             double bv = -1.0;
-            for (int k = j; k < p; ++k) {
-                double d = A[(long long)piv[k] * p + piv[k]];
+            for (int k = j + t; k < p; k += 32) {
+                const double d = A[(long long)piv[k] * p + piv[k]];
                 if (d > bv) { bv = d; best = k; }
             }
-            if (j == 0) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+                const int ob = __shfl_down_sync(0xffffffffu, best, off);
+                if (ov > bv || (ov == bv && ob >= 0 && (best < 0 || ob < best))) { bv = ov; best = ob; }
+            }
+            bv = __shfl_sync(0xffffffffu, bv, 0);
+            best = __shfl_sync(0xffffffffu, best, 0);
+            if (t == 0 && j == 0) {
                 s_d0 = bv;
                 if (!(bv > 0.0) || !isfinite(bv)) *flag = 1;
             }
-            if (best < 0 || !(bv > tol * tol * s_d0)) {
-                s_r = j;
-                s_go = 0;
-            } else {
-                int tmp = piv[j];
-                piv[j] = piv[best];
-                piv[best] = tmp;
-                for (int i = 0; i < j; ++i) {      // the finished rows of R follow the swap
-                    double x = R[(long long)i * p + j];
+            __syncwarp();
+            const bool go = best >= 0 && bv > tol * tol * s_d0;
+            if (go) {
+                for (int i = t; i < j; i += 32) {  // the finished rows of R follow the swap
+                    const double x = R[(long long)i * p + j];
                     R[(long long)i * p + j] = R[(long long)i * p + best];
                     R[(long long)i * p + best] = x;
                 }
-                s_d = sqrt(bv);
-                R[(long long)j * p + j] = s_d;
-                s_go = 1;
+            }
+            if (t == 0) {
+                if (!go) {
+                    s_r = j;
+                    s_go = 0;
+                } else {
+                    const int tmp = piv[j];
+                    piv[j] = piv[best];
+                    piv[best] = tmp;
+                    s_d = sqrt(bv);
+                    R[(long long)j * p + j] = s_d;
+                    s_go = 1;
+                }
             }
         }
         __syncthreads();
         if (!s_go) break;
         const int pj = piv[j];
-        const double d = s_d;
-        for (int k = j + 1 + t; k < p; k += nt) R[(long long)j * p + k] = A[(long long)pj * p + piv[k]] / d;
+        const double dinv = 1.0 / s_d;
+        for (int k = j + 1 + t; k < p; k += nt) R[(long long)j * p + k] = A[(long long)pj * p + piv[k]] * dinv;
         __syncthreads();
         const int m = p - j - 1;
         for (int q = t; q < m * m; q += nt) {
@@ -525,13 +488,18 @@ __global__ void gram_pivchol_kernel(const double *__restrict__ G, int p, double 
         __syncthreads();
     }
     const int r = s_r;
-    // R11^-1 (upper, r x r) by back substitution, one column per thread
-    for (int c = t; c < r; c += nt)
-        for (int i = r - 1; i >= 0; --i) {
+    // R11^-1 (upper, r x r) by back substitution, one column per thread,
+    // multiplying by the reciprocals of the diagonal (kept in A, free now)
+    for (int i = t; i < r; i += nt) A[i] = 1.0 / R[(long long)i * p + i];
+    __syncthreads();
+    for (int c = t; c < r; c += nt) {
+        for (int i = r - 1; i > c; --i) Ri[(long long)i * r + c] = 0.0;
+        for (int i = c; i >= 0; --i) {
             double sacc = (i == c) ? 1.0 : 0.0;
             for (int k = i + 1; k <= c; ++k) sacc -= R[(long long)i * p + k] * Ri[(long long)k * r + c];
-            Ri[(long long)i * r + c] = sacc / R[(long long)i * p + i];
+            Ri[(long long)i * r + c] = sacc * A[i];
         }
+    }
     for (long long q = t; q < (long long)r * p; q += nt) coef[q] = 0.f;
     __syncthreads();
     // coef[a][piv[b]] = (R11^-T)[a][b] = R11^-1[b][a]
@@ -542,14 +510,42 @@ __global__ void gram_pivchol_kernel(const double *__restrict__ G, int p, double 
     if (t == 0) *r_out = r;
 }
 
+// Eigenpairs of the Jacobi result (eigenvalues on the diagonal of Af,
+// eigenvectors in the columns of Uf, r x r) ordered by |lambda| descending
+// (the first index among equal magnitudes): lam[k] and coef [rank][r] = U^T,
+// zero beyond r.  Each eigenvalue's position is its count of larger ones, so
+// every thread places its own.  A non-finite eigenvalue sets flag 4.
+__device__ void select_eigenpairs(const float *Af, const float *Uf, int r, int rank, double *__restrict__ lam,
+                                  float *__restrict__ coef, int *__restrict__ flag)
+{
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int i = t; i < r; i += nt) {
+        const float vi = fabsf(Af[(long long)i * r + i]);
+        if (!isfinite(vi)) *flag = 4;
+        int pos = 0;
+        for (int j = 0; j < r; ++j) {
+            const float vj = fabsf(Af[(long long)j * r + j]);
+            pos += (vj > vi || (vj == vi && j < i)) ? 1 : 0;
+        }
+        if (pos < rank) {
+            lam[pos] = (double)Af[(long long)i * r + i];
+            for (int a = 0; a < r; ++a) coef[(long long)pos * r + a] = Uf[(long long)a * r + i];
+        }
+    }
+    for (int q = t; q < (rank - min(rank, r)) * r; q += nt) coef[(long long)min(rank, r) * r + q] = 0.f;
+    for (int k = r + t; k < rank; k += nt) lam[k] = 0.0;
+}
+
 // Single-pass randomized SVD core (Algorithm 3) with r <= p basis vectors:
-// Omega (Q^T X) = Q^T E solved in the least-squares sense,
-// Omega = QE QX^T (QX QX^T)^-1 (= QE QX^-1 when r = p), symmetrised, then
-// eigendecomposed; eigenpairs by |lambda| descending.  QE, QX: [r][p] FP64.
+// Omega (Q^T X) = Q^T E, solved directly when r = p (Omega = QE QX^-1) and
+// in the least-squares sense Omega = QE QX^T (QX QX^T)^-1 when r < p
+// (Gauss-Jordan with partial pivoting in FP64), symmetrised, then
+// eigendecomposed; eigenpairs by |lambda| descending.  QE, QX: [r][p] FP64
+// with row stride ldq.
 // Outputs lam[rank] (zeros beyond r) and coef[rank][r] = U^T (zero rows
 // beyond r).  work: >= 4 r^2 + 4 r doubles (or shared memory).
-__global__ void omega_ls_kernel(const double *__restrict__ QE, const double *__restrict__ QX, int r, int p,
-                                int rank, double *work, double *__restrict__ lam, float *__restrict__ coef,
+__global__ void omega_ls_kernel(const double *__restrict__ QE, const double *__restrict__ QX, long long ldq, int r,
+                                int p, int rank, double *work, double *__restrict__ lam, float *__restrict__ coef,
                                 int *__restrict__ flag, int use_smem)
 {
     extern __shared__ double smem_work[];
@@ -560,28 +556,47 @@ __global__ void omega_ls_kernel(const double *__restrict__ QE, const double *__r
     double *U = A + (long long)r * r;       // [r][r]
     double *cs = U + (long long)r * r;      // >= r + 1
     __shared__ int piv_row;
-    for (int q = t; q < r * r; q += nt) {
-        int i = q / r, j = q % r;
-        double nij = 0.0, bji = 0.0;
-        for (int c = 0; c < p; ++c) {
-            nij += QX[(long long)i * p + c] * QX[(long long)j * p + c];
-            bji += QE[(long long)j * p + c] * QX[(long long)i * p + c];   // Bm[j][i]
+    if (r == p) {
+        // square Q^T X: solve (Q^T X)^T Omega^T = (Q^T E)^T directly
+        for (int q = t; q < r * r; q += nt) {
+            const int i = q / r, j = q % r;
+            Aug[(long long)i * 2 * r + j] = QX[(long long)j * ldq + i];
+            Aug[(long long)i * 2 * r + r + j] = QE[(long long)j * ldq + i];
         }
-        Aug[(long long)i * 2 * r + j] = nij;
-        Aug[(long long)i * 2 * r + r + j] = bji;                          // Bm^T[i][j]
+    } else {
+        // least squares through the normal equations of the wide Q^T X
+        for (int q = t; q < r * r; q += nt) {
+            const int i = q / r, j = q % r;
+            double nij = 0.0, bji = 0.0;
+            for (int c = 0; c < p; ++c) {
+                nij += QX[(long long)i * ldq + c] * QX[(long long)j * ldq + c];
+                bji += QE[(long long)j * ldq + c] * QX[(long long)i * ldq + c];   // Bm[j][i]
+            }
+            Aug[(long long)i * 2 * r + j] = nij;
+            Aug[(long long)i * 2 * r + r + j] = bji;                          // Bm^T[i][j]
+        }
     }
     __syncthreads();
     // Gauss-Jordan with partial pivoting: N Omega^T = Bm^T
     for (int j = 0; j < r; ++j) {
-        if (t == 0) {
-            int best = j;
-            double bv = fabs(Aug[(long long)j * 2 * r + j]);
-            for (int rr = j + 1; rr < r; ++rr) {
-                double v = fabs(Aug[(long long)rr * 2 * r + j]);
+        if (t < 32) {
+            // partial pivot (first row among equals), warp 0
+            int best = -1;
+            double bv = -1.0;
+            for (int rr = j + t; rr < r; rr += 32) {
+                const double v = fabs(Aug[(long long)rr * 2 * r + j]);
                 if (v > bv) { bv = v; best = rr; }
             }
-            if (!(bv > 0.0)) *flag = 3;
-            piv_row = best;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+                const int ob = __shfl_down_sync(0xffffffffu, best, off);
+                if (ov > bv || (ov == bv && ob >= 0 && (best < 0 || ob < best))) { bv = ov; best = ob; }
+            }
+            if (t == 0) {
+                if (!(bv > 0.0)) *flag = 3;
+                piv_row = best < 0 ? j : best;
+            }
         }
         __syncthreads();
         int pr = piv_row;
@@ -594,8 +609,9 @@ __global__ void omega_ls_kernel(const double *__restrict__ QE, const double *__r
         __syncthreads();
         double d = Aug[(long long)j * 2 * r + j];
         if (d == 0.0) d = 1.0;
+        const double dinv = 1.0 / d;
         __syncthreads();
-        for (int c = t; c < 2 * r; c += nt) Aug[(long long)j * 2 * r + c] /= d;
+        for (int c = t; c < 2 * r; c += nt) Aug[(long long)j * 2 * r + c] *= dinv;
         __syncthreads();
         for (int q = t; q < r * 2 * r; q += nt) {
             int rr = q / (2 * r), c = q % (2 * r);
@@ -619,32 +635,8 @@ __global__ void omega_ls_kernel(const double *__restrict__ QE, const double *__r
         Af[q] = (float)(0.5 * (oij + oji));
         Uf[q] = (i == j) ? 1.f : 0.f;
     }
-    block_jacobi<float>(Af, Uf, r, csf, 60);
-    if (t == 0) {
-        int *used = reinterpret_cast<int *>(cs);
-        for (int i = 0; i < r; ++i) used[i] = 0;
-        for (int k = 0; k < rank; ++k) {
-            if (k >= r) {
-                lam[k] = 0.0;
-                for (int a2 = 0; a2 < r; ++a2) coef[(long long)k * r + a2] = 0.f;
-                continue;
-            }
-            int best = -1;
-            float bv = -1.f;
-            for (int i = 0; i < r; ++i) {
-                if (used[i]) continue;
-                float v = fabsf(Af[(long long)i * r + i]);
-                if (v > bv) { bv = v; best = i; }
-            }
-            if (best < 0) {                     // non-finite diagonal
-                *flag = 4;
-                for (best = 0; used[best]; ++best) {}
-            }
-            used[best] = 1;
-            lam[k] = (double)Af[(long long)best * r + best];
-            for (int a2 = 0; a2 < r; ++a2) coef[(long long)k * r + a2] = Uf[(long long)a2 * r + best];
-        }
-    }
+    block_jacobi<float>(Af, Uf, r, csf, reinterpret_cast<short *>(A), 40);
+    select_eigenpairs(Af, Uf, r, rank, lam, coef, flag);
 }
 
 // d_i = 1 / sqrt(G_ii) (0 for an empty row), G <- D G D: the pivoted
@@ -694,7 +686,7 @@ __global__ void exact_t_kernel(const double *__restrict__ C, const double *__res
 
 // Eigenpairs of a symmetric r x r matrix T (FP32 block Jacobi), ordered by
 // |lambda| descending: lam[rank] and coef [rank][r] = U^T (zero rows
-// beyond r).  work: >= r^2 + r + 8 doubles (or shared memory).
+// beyond r).  work: >= r^2 + r + 16 + (r + 2)^2 / 4 doubles (or shared memory).
 __global__ void eig_select_kernel(const double *__restrict__ T, int r, int rank, double *work,
                                   double *__restrict__ lam, float *__restrict__ coef, int *__restrict__ flag,
                                   int use_smem)
@@ -705,39 +697,16 @@ __global__ void eig_select_kernel(const double *__restrict__ T, int r, int rank,
     float *Af = reinterpret_cast<float *>(work);
     float *Uf = Af + (long long)r * r;
     float *csf = Uf + (long long)r * r;            // >= r + 2 floats
+    short *pairs = reinterpret_cast<short *>(csf + r + 2);   // (r + 1)^2 shorts
     for (int q = t; q < r * r; q += nt) {
         Af[q] = (float)T[q];
         Uf[q] = (q / r == q % r) ? 1.f : 0.f;
     }
-    block_jacobi<float>(Af, Uf, r, csf, 60);
-    if (t == 0) {
-        int *used = reinterpret_cast<int *>(csf);
-        for (int i = 0; i < r; ++i) used[i] = 0;
-        for (int k = 0; k < rank; ++k) {
-            if (k >= r) {
-                lam[k] = 0.0;
-                for (int a = 0; a < r; ++a) coef[(long long)k * r + a] = 0.f;
-                continue;
-            }
-            int best = -1;
-            float bv = -1.f;
-            for (int i = 0; i < r; ++i) {
-                if (used[i]) continue;
-                float v = fabsf(Af[(long long)i * r + i]);
-                if (v > bv) { bv = v; best = i; }
-            }
-            if (best < 0) {
-                *flag = 4;
-                for (best = 0; used[best]; ++best) {}
-            }
-            used[best] = 1;
-            lam[k] = (double)Af[(long long)best * r + best];
-            for (int a = 0; a < r; ++a) coef[(long long)k * r + a] = Uf[(long long)a * r + best];
-        }
-    }
+    block_jacobi<float>(Af, Uf, r, csf, pairs, 40);
+    select_eigenpairs(Af, Uf, r, rank, lam, coef, flag);
 }
 
-__global__ void std_kernel(const float *__restrict__ V, const double *__restrict__ lam, int rank,
+__global__ void std_kernel(const float *__restrict__ V, long long ldv, const double *__restrict__ lam, int rank,
                            const float *__restrict__ B0, long long n, float eps, float *__restrict__ out)
 {
     __shared__ float sl[256];
@@ -747,7 +716,7 @@ __global__ void std_kernel(const float *__restrict__ V, const double *__restrict
          i += (long long)gridDim.x * blockDim.x) {
         float s = B0[i];
         for (int r = 0; r < rank; ++r) {
-            float v = V[(long long)r * n + i];
+            float v = V[(long long)r * ldv + i];
             s = fmaf(sl[r] * v, v, s);
         }
         out[i] = sqrtf(eps * fmaxf(s, 0.f));
@@ -768,7 +737,10 @@ __device__ __forceinline__ void philox10(unsigned c[4], unsigned k0, unsigned k1
     }
 }
 
-__global__ void philox_normal_kernel(float *__restrict__ X, long long total, unsigned long long seed)
+// element e = row * n + col of the [p][n] probe block (the counter is e / 4)
+// is stored at X[row * ld + col]
+__global__ void philox_normal_kernel(float *__restrict__ X, long long total, long long n, long long ld,
+                                     unsigned long long seed)
 {
     const float two_pi = 6.28318530717958647692f;
     for (long long blk = blockIdx.x * (long long)blockDim.x + threadIdx.x; blk * 4 < total;
@@ -783,86 +755,97 @@ __global__ void philox_normal_kernel(float *__restrict__ X, long long total, uns
             float sn, cn;
             sincosf(two_pi * u2, &sn, &cn);
             long long e = blk * 4 + 2 * pr;
-            if (e < total) X[e] = rad * cn;
-            if (e + 1 < total) X[e + 1] = rad * sn;
+            if (e < total) X[(e / n) * ld + e % n] = rad * cn;
+            if (e + 1 < total) X[((e + 1) / n) * ld + (e + 1) % n] = rad * sn;
         }
     }
 }
 
 int grid_n(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 8); }
 
-// C[a][b] = sum_i A[a][i] w[i] Bm[b][i] -> out (device FP64, row stride ldo)
-int atb(gbfwi_bfgs *h, const float *A, long long lda, int ka, const float *Bm, long long ldb, int kb,
-        const float *w, double *out, long long ldo, cudaStream_t s, bool accurate = false)
+// splits of the one- and two-column products
+long long thin_splits(long long n) { return std::min<long long>(304, std::max<long long>(1, (n + 4095) / 4096)); }
+
+// FP64 split-K partials an (ka x kb) product of this store takes
+size_t part_need(const gbfwi_bfgs *h, int ka, int kb)
 {
-    if (ka == 0 || kb == 0) return GBFWI_OK;
-    const long long n = h->n;
-    long long nsplit = std::min<long long>(304, std::max<long long>(1, (n + 4095) / 4096));
-    long long chunk = ((n + nsplit - 1) / nsplit + KI - 1) / KI * KI;
-    nsplit = (n + chunk - 1) / chunk;
-    GB_TRY(h->part.ensure((size_t)nsplit * ka * kb * sizeof(double)));
-    if (kb <= 2) {
-        // one or two columns: a thin, always compensated pass
-        dim3 tg((unsigned)nsplit, (unsigned)ka);
-        if (kb == 1)
-            atb_thin<1><<<tg, 256, 0, s>>>(A, lda, Bm, ldb, w, n, chunk, ka, h->part.as<double>());
-        else
-            atb_thin<2><<<tg, 256, 0, s>>>(A, lda, Bm, ldb, w, n, chunk, ka, h->part.as<double>());
-        GB_LAUNCHED();
-        int nab = ka * kb;
-        atb_reduce<<<(nab + 255) / 256, 256, 0, s>>>(h->part.as<double>(), (int)nsplit, nab, out, ldo, kb);
-        GB_LAUNCHED();
-        return GBFWI_OK;
-    }
-    dim3 grid((unsigned)nsplit, (ka + AT - 1) / AT, (kb + AT - 1) / AT);
-    if (accurate)
-        atb_partial<true><<<grid, 256, 0, s>>>(A, lda, ka, Bm, ldb, kb, w, n, chunk, h->part.as<double>());
-    else
-        atb_partial<false><<<grid, 256, 0, s>>>(A, lda, ka, Bm, ldb, kb, w, n, chunk, h->part.as<double>());
-    GB_LAUNCHED();
-    int nab = ka * kb;
-    atb_reduce<<<(nab + 255) / 256, 256, 0, s>>>(h->part.as<double>(), (int)nsplit, nab, out, ldo, kb);
-    GB_LAUNCHED();
-    return GBFWI_OK;
+    if (ka < 1 || kb < 1) return 0;
+    if (kb <= 2) return (size_t)thin_splits(h->n) * ka * kb;
+    const long long ns = gb_tc_atb_splits(ka, kb, h->n);
+    return ns < 1 ? 0 : (size_t)ns * ka * kb;
 }
 
-// out[c] = sum_a coef[c][a] row_a + beta * dw * Xc[c], c < nc
-int combine(gbfwi_bfgs *h, const float *A1, const float *A2, int k1, int ktot, const float *coef, int nc,
-            float *out, const float *dw, const float *Xc, float beta, cudaStream_t s)
+// out[a][b] = sum_i A_a[i] B_b[i] -> out (device FP64, row stride ldo); the
+// A rows a < ka1 come from A1, the rest from A2 (likewise B).  Rows have the
+// store's pitch.  One or two columns from a single B block: compensated
+// CUDA-core dot products; otherwise the tensor-core 3xTF32 product.
+int atb(gbfwi_bfgs *h, const float *A1, const float *A2, int ka1, int ka, const float *B1, const float *B2, int kb1,
+        int kb, double *out, long long ldo, cudaStream_t s)
 {
-    const long long n = h->n;
+    if (ka == 0 || kb == 0) return GBFWI_OK;
+    const long long n = h->n, ld = h->ld;
+    if (kb <= 2 && kb1 >= kb) {
+        const long long nsplit = thin_splits(n);
+        const long long chunk = (n + nsplit - 1) / nsplit;
+        const long long ns = (n + chunk - 1) / chunk;
+        for (int blk = 0; blk < 2; ++blk) {
+            const float *A = blk == 0 ? A1 : A2;
+            const int kab = blk == 0 ? std::min(ka1, ka) : ka - ka1;
+            if (kab <= 0) continue;
+            if ((size_t)ns * kab * kb > h->part.bytes / sizeof(double)) return GBFWI_EINVAL;
+            dim3 tg((unsigned)ns, (unsigned)kab);
+            if (kb == 1)
+                atb_thin<1><<<tg, 256, 0, s>>>(A, ld, B1, ld, nullptr, n, chunk, kab, h->part.as<double>());
+            else
+                atb_thin<2><<<tg, 256, 0, s>>>(A, ld, B1, ld, nullptr, n, chunk, kab, h->part.as<double>());
+            GB_LAUNCHED();
+            const int nab = kab * kb;
+            atb_reduce<<<(nab + 255) / 256, 256, 0, s>>>(h->part.as<double>(), (int)ns, nab,
+                                                         out + (blk == 0 ? 0 : (long long)ka1 * ldo), ldo, kb);
+            GB_LAUNCHED();
+        }
+        return GBFWI_OK;
+    }
+    return gb_tc_atb(A1, A2, ka1, ka, B1, B2, kb1, kb, ld, n, h->part.as<double>(), h->part.bytes / sizeof(double),
+                     out, ldo, s);
+}
+
+// out[c] = sum_a coef[c][a] row_a + beta * dw * Xc[c], c < nc; rows a < k1
+// from A1, the rest from A2 (pitch ld); out and Xc with their own pitches
+int combine(gbfwi_bfgs *h, const float *A1, const float *A2, int k1, int ktot, const float *coef, int nc,
+            float *out, long long ldo, const float *dw, const float *Xc, long long ldx, float beta, cudaStream_t s)
+{
+    const long long n = h->n, ld = h->ld;
+    if (ktot >= 1 && ktot <= 128)
+        return gb_tc_combine(A1, A2, k1, ktot, ld, coef, nc, n, out, ldo, dw, Xc, ldx, beta, s);
+    // no rows (out = beta dw Xc) or more than 128: CUDA-core combination
     for (int c0 = 0; c0 < nc; c0 += 64) {
         int cn = std::min(64, nc - c0);
         size_t smem = (size_t)std::max(ktot, 1) * 64 * sizeof(float);
-        if (cn <= 16) {
-            smem = (size_t)std::max(ktot, 1) * 16 * sizeof(float);
-            if (smem > 48 * 1024)
-                GB_CUDA(cudaFuncSetAttribute(combine_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            combine_kernel<16><<<grid_n(n) / 2 + 1, 128, smem, s>>>(A1, A2, k1, ktot, n, coef, c0, cn, n, out, n, dw,
-                                                                  Xc, n, beta);
-        } else if (cn <= 32) {
-            smem = (size_t)std::max(ktot, 1) * 32 * sizeof(float);
-            if (smem > 48 * 1024)
-                GB_CUDA(cudaFuncSetAttribute(combine_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            combine_kernel<32><<<grid_n(n) / 2 + 1, 128, smem, s>>>(A1, A2, k1, ktot, n, coef, c0, cn, n, out, n, dw,
-                                                                  Xc, n, beta);
-        } else {
-            if (smem > 48 * 1024)
-                GB_CUDA(cudaFuncSetAttribute(combine_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            combine_kernel<64><<<grid_n(n) / 2 + 1, 128, smem, s>>>(A1, A2, k1, ktot, n, coef, c0, cn, n, out, n, dw,
-                                                                  Xc, n, beta);
-        }
+        if (smem > 48 * 1024)
+            GB_CUDA(cudaFuncSetAttribute(combine_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        combine_kernel<64><<<grid_n(n) / 2 + 1, 128, smem, s>>>(A1, A2, k1, ktot, ld, coef, c0, cn, n, out, ldo, dw,
+                                                              Xc, ldx, beta);
         GB_LAUNCHED();
     }
     return GBFWI_OK;
 }
 
-int stage_in(DevBuf &buf, const float *user, size_t count, cudaStream_t s, const float **dptr)
+// Copy a caller's [rows][n] block (host or device, contiguous rows) into a
+// store buffer with the store's pitch.
+int stage_rows(gbfwi_bfgs *h, DevBuf &buf, const float *user, int rows, cudaStream_t s)
 {
-    if (gb_is_device_ptr(user)) { *dptr = user; return GBFWI_OK; }
-    GB_TRY(buf.ensure(count * sizeof(float)));
-    GB_CUDA(cudaMemcpyAsync(buf.p, user, count * sizeof(float), cudaMemcpyHostToDevice, s));
-    *dptr = buf.as<float>();
+    GB_TRY(buf.ensure((size_t)rows * h->ld * sizeof(float)));
+    GB_CUDA(cudaMemcpy2DAsync(buf.p, h->ld * sizeof(float), user, h->n * sizeof(float), h->n * sizeof(float), rows,
+                              cudaMemcpyDefault, s));
+    return GBFWI_OK;
+}
+
+// Copy rows of a store buffer (pitch ld) out to a caller's contiguous block
+int unstage_rows(gbfwi_bfgs *h, float *user, const float *dev, int rows, cudaStream_t s)
+{
+    GB_CUDA(cudaMemcpy2DAsync(user, h->n * sizeof(float), dev, h->ld * sizeof(float), h->n * sizeof(float), rows,
+                              cudaMemcpyDefault, s));
     return GBFWI_OK;
 }
 
@@ -871,43 +854,64 @@ size_t small_apply_doubles(const gbfwi_bfgs *h, int p) { return (size_t)4 * std:
 
 // Size the scratch buffers once per call so that nothing is reallocated
 // while kernels queued earlier in the same call may still use it.
-int reserve(gbfwi_bfgs *h, int p, bool lowrank)
+// shapes: the (ka, kb) of every product the call makes.
+int reserve(gbfwi_bfgs *h, int p, bool lowrank, std::initializer_list<std::pair<int, int>> shapes)
 {
-    const long long n = h->n;
-    long long nsplit = std::min<long long>(304, std::max<long long>(1, (n + 4095) / 4096));
-    size_t ab = std::max<size_t>({(size_t)(h->k + 1) * 2, (size_t)std::max(h->k, 1) * p, (size_t)p * p});
-    GB_TRY(h->part.ensure((size_t)(nsplit + 1) * ab * sizeof(double)));
+    size_t part = 16;
+    for (const auto &sh : shapes) part = std::max(part, part_need(h, sh.first, sh.second));
+    GB_TRY(h->part.ensure(part * sizeof(double)));
     size_t pp = (size_t)p * p;
-    size_t sm = small_apply_doubles(h, p) + (lowrank ? pp * 10 + 8 * (size_t)p + 64 : 0);
+    size_t sm = small_apply_doubles(h, p) + (lowrank ? pp * 12 + 8 * (size_t)p + 64 : 0);
     sm = std::max(sm, (size_t)(4 * (h->k + 1) + 8));
     GB_TRY(h->small.ensure(sm * sizeof(double)));
     GB_TRY(h->coef.ensure(std::max<size_t>({pp, (size_t)p * 2 * std::max(h->k, 1), 16}) * sizeof(float)));
     return GBFWI_OK;
 }
 
-// Z = (H - minus_B0 gamma B0) X into the device buffer Z ([p][n])
-int apply_dev(gbfwi_bfgs *h, const float *Xd, int p, float *Zd, double gamma, int minus_B0, cudaStream_t s,
-              bool accurate = false)
+// Z = (H - minus_B0 gamma B0) X for X [p] rows of pitch ldx into Z (pitch
+// ldz).  For p >= 3 the rows of X must be 16-byte aligned with ldx a
+// multiple of 4 (a store buffer).
+int apply_dev(gbfwi_bfgs *h, const float *Xd, long long ldx, int p, float *Zd, long long ldz, double gamma,
+              int minus_B0, cudaStream_t s)
 {
-    const long long n = h->n;
     const int k = h->k;
     float beta = minus_B0 ? 0.f : (float)gamma;
     if (k == 0) {
         if (beta == 0.f) {
-            GB_CUDA(cudaMemsetAsync(Zd, 0, (size_t)p * n * sizeof(float), s));
+            GB_CUDA(cudaMemset2DAsync(Zd, ldz * sizeof(float), 0, h->n * sizeof(float), p, s));
             return GBFWI_OK;
         }
-        return combine(h, nullptr, nullptr, 0, 0, nullptr, p, Zd, h->B0.as<float>(), Xd, beta, s);
+        return combine(h, nullptr, nullptr, 0, 0, nullptr, p, Zd, ldz, h->B0.as<float>(), Xd, ldx, beta, s);
     }
     double *T = h->small.as<double>();
     double *scr = T + 2 * k * p;
-    GB_TRY(atb(h, h->S.as<float>(), n, k, Xd, n, p, nullptr, T, p, s, accurate));
-    GB_TRY(atb(h, h->BY.as<float>(), n, k, Xd, n, p, nullptr, T + (long long)k * p, p, s, accurate));
+    // T = [S; B0 Y] X^T: rows 0..k-1 S^T x_c, rows k..2k-1 (B0 Y)^T x_c, one pass over X
+    if (p <= 2 && ldx != h->ld) {
+        // a caller's one or two vectors with their own pitch: thin products
+        const long long n = h->n;
+        const long long nsplit = thin_splits(n);
+        const long long chunk = (n + nsplit - 1) / nsplit;
+        const long long ns = (n + chunk - 1) / chunk;
+        for (int blk = 0; blk < 2; ++blk) {
+            const float *A = blk == 0 ? h->S.as<float>() : h->BY.as<float>();
+            dim3 tg((unsigned)ns, (unsigned)k);
+            if (p == 1)
+                atb_thin<1><<<tg, 256, 0, s>>>(A, h->ld, Xd, ldx, nullptr, n, chunk, k, h->part.as<double>());
+            else
+                atb_thin<2><<<tg, 256, 0, s>>>(A, h->ld, Xd, ldx, nullptr, n, chunk, k, h->part.as<double>());
+            GB_LAUNCHED();
+            atb_reduce<<<(k * p + 255) / 256, 256, 0, s>>>(h->part.as<double>(), (int)ns, k * p,
+                                                           T + (long long)blk * k * p, p, p);
+            GB_LAUNCHED();
+        }
+    } else {
+        GB_TRY(atb(h, h->S.as<float>(), h->BY.as<float>(), k, 2 * k, Xd, nullptr, p, p, T, p, s));
+    }
     middle_kernel<<<(p + 63) / 64, 64, 0, s>>>(T, h->dSY.as<double>(), h->dYBY.as<double>(), k, h->kmax, p, gamma,
                                                scr, h->coef.as<float>());
     GB_LAUNCHED();
-    return combine(h, h->S.as<float>(), h->BY.as<float>(), k, 2 * k, h->coef.as<float>(), p, Zd,
-                   h->B0.as<float>(), Xd, beta, s);
+    return combine(h, h->S.as<float>(), h->BY.as<float>(), k, 2 * k, h->coef.as<float>(), p, Zd, ldz,
+                   h->B0.as<float>(), Xd, ldx, beta, s);
 }
 
 }  // namespace
@@ -923,10 +927,12 @@ extern "C" int gbfwi_bfgs_create(long long n, int kmax, const float *B0, gbfwi_b
     gbfwi_bfgs *h = new (std::nothrow) gbfwi_bfgs();
     if (!h) return GBFWI_ENOMEM;
     h->n = n;
+    h->ld = (n + 63) / 64 * 64;
     h->kmax = kmax;
-    int rc = h->S.ensure((size_t)kmax * n * sizeof(float));
-    if (!rc) rc = h->Y.ensure((size_t)kmax * n * sizeof(float));
-    if (!rc) rc = h->BY.ensure((size_t)kmax * n * sizeof(float));
+    const size_t store = (size_t)kmax * h->ld * sizeof(float);
+    int rc = h->S.ensure(store);
+    if (!rc) rc = h->Y.ensure(store);
+    if (!rc) rc = h->BY.ensure(store);
     if (!rc) rc = h->B0.ensure((size_t)n * sizeof(float));
     if (!rc) rc = h->dSY.ensure((size_t)kmax * kmax * sizeof(double));
     if (!rc) rc = h->dYBY.ensure((size_t)kmax * kmax * sizeof(double));
@@ -934,9 +940,11 @@ extern "C" int gbfwi_bfgs_create(long long n, int kmax, const float *B0, gbfwi_b
     if (rc) { delete h; return rc; }
     h->SY.assign((size_t)kmax * kmax, 0.0);
     h->YBY.assign((size_t)kmax * kmax, 0.0);
-    cudaMemcpyKind kind = gb_is_device_ptr(B0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if (cudaMemcpy(h->B0.p, B0, (size_t)n * sizeof(float), kind) != cudaSuccess) {
-        gb_set_last_cuda_error(cudaGetLastError(), "copy B0", __FILE__, __LINE__);
+    // the row padding stays zero
+    if (cudaMemset(h->S.p, 0, store) != cudaSuccess || cudaMemset(h->Y.p, 0, store) != cudaSuccess ||
+        cudaMemset(h->BY.p, 0, store) != cudaSuccess ||
+        cudaMemcpy(h->B0.p, B0, (size_t)n * sizeof(float), cudaMemcpyDefault) != cudaSuccess) {
+        gb_set_last_cuda_error(cudaGetLastError(), "initialise the BFGS store", __FILE__, __LINE__);
         delete h;
         return GBFWI_ECUDA;
     }
@@ -958,26 +966,25 @@ extern "C" int gbfwi_bfgs_update(gbfwi_bfgs *h, const float *s_, const float *y_
     GB_TRY(gb_check_local(s_, y_));
     if (h->k >= h->kmax) return GBFWI_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    const long long n = h->n;
+    const long long n = h->n, ld = h->ld;
     const int k = h->k;
-    float *sk = h->S.as<float>() + (long long)k * n;
-    float *yk = h->Y.as<float>() + (long long)k * n;
-    float *byk = h->BY.as<float>() + (long long)k * n;
-    GB_CUDA(cudaMemcpyAsync(sk, s_, n * sizeof(float), gb_is_device_ptr(s_) ? cudaMemcpyDeviceToDevice
-                                                                              : cudaMemcpyHostToDevice, s));
-    GB_CUDA(cudaMemcpyAsync(yk, y_, n * sizeof(float), gb_is_device_ptr(y_) ? cudaMemcpyDeviceToDevice
-                                                                              : cudaMemcpyHostToDevice, s));
+    float *sk = h->S.as<float>() + (long long)k * ld;
+    float *yk = h->Y.as<float>() + (long long)k * ld;
+    float *byk = h->BY.as<float>() + (long long)k * ld;
+    GB_CUDA(cudaMemcpyAsync(sk, s_, n * sizeof(float), cudaMemcpyDefault, s));
+    GB_CUDA(cudaMemcpyAsync(yk, y_, n * sizeof(float), cudaMemcpyDefault, s));
     mul_kernel<<<grid_n(n), 256, 0, s>>>(h->B0.as<float>(), yk, n, byk);
     GB_LAUNCHED();
     // dots: s_i^T [y_k, s_k] (i <= k), (B0 y_i)^T y_k (i <= k), y_k^T y_k
-    GB_TRY(reserve(h, 1, false));
+    GB_TRY(reserve(h, 1, false, {{k + 1, 1}}));
     double *d1 = h->small.as<double>();          // [(k+1)][2]
     double *d2 = d1 + 2 * (k + 1);               // [(k+1)]
     double *d3 = d2 + (k + 1);                   // [1]
-    GB_TRY(atb(h, h->S.as<float>(), n, k + 1, yk, n, 1, nullptr, d1, 2, s));
-    GB_TRY(atb(h, h->S.as<float>(), n, k + 1, sk, n, 1, nullptr, d1 + 1, 2, s));
-    GB_TRY(atb(h, h->BY.as<float>(), n, k + 1, yk, n, 1, nullptr, d2, 1, s));
-    GB_TRY(atb(h, yk, n, 1, yk, n, 1, nullptr, d3, 1, s));
+    const float *S = h->S.as<float>(), *BY = h->BY.as<float>();
+    GB_TRY(atb(h, S, nullptr, k + 1, k + 1, yk, nullptr, 1, 1, d1, 2, s));
+    GB_TRY(atb(h, S, nullptr, k + 1, k + 1, sk, nullptr, 1, 1, d1 + 1, 2, s));
+    GB_TRY(atb(h, BY, nullptr, k + 1, k + 1, yk, nullptr, 1, 1, d2, 1, s));
+    GB_TRY(atb(h, yk, nullptr, 1, 1, yk, nullptr, 1, 1, d3, 1, s));
     std::vector<double> hd(4 * (k + 1) + 1);
     GB_CUDA(cudaMemcpyAsync(hd.data(), d1, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
@@ -1004,19 +1011,28 @@ extern "C" int gbfwi_bfgs_apply(gbfwi_bfgs *h, const float *X, int p, float *Z, 
     if (!h || !X || !Z || p < 1 || p > 256 || !(gamma > 0)) return GBFWI_EINVAL;
     GB_TRY(gb_check_local(X, Z));
     cudaStream_t s = (cudaStream_t)stream;
-    const long long n = h->n;
-    const float *Xd;
-    GB_TRY(stage_in(h->X, X, (size_t)p * n, s, &Xd));
-    GB_TRY(reserve(h, p, false));
+    const long long n = h->n, ld = h->ld;
+    const int k = h->k;
+    GB_TRY(reserve(h, p, false, {{2 * k, p}, {k, p}}));
+    const float *Xd = X;
+    long long ldx = n;
+    if (p >= 3 || !gb_is_device_ptr(X)) {
+        // a block goes to the tensor cores from a store buffer (aligned rows)
+        GB_TRY(stage_rows(h, h->X, X, p, s));
+        Xd = h->X.as<float>();
+        ldx = ld;
+    }
     const bool dev_out = gb_is_device_ptr(Z);
     float *Zd = Z;
+    long long ldz = n;
     if (!dev_out) {
-        GB_TRY(h->E.ensure((size_t)p * n * sizeof(float)));
+        GB_TRY(h->E.ensure((size_t)p * ld * sizeof(float)));
         Zd = h->E.as<float>();
+        ldz = ld;
     }
-    GB_TRY(apply_dev(h, Xd, p, Zd, gamma, minus_B0, s));
+    GB_TRY(apply_dev(h, Xd, ldx, p, Zd, ldz, gamma, minus_B0, s));
     if (!dev_out) {
-        GB_CUDA(cudaMemcpyAsync(Z, Zd, (size_t)p * n * sizeof(float), cudaMemcpyDeviceToHost, s));
+        GB_TRY(unstage_rows(h, Z, Zd, p, s));
         GB_CUDA(cudaStreamSynchronize(s));
     }
     return GBFWI_OK;
@@ -1028,30 +1044,31 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
     if (!h || p < 1 || p > 256 || rank < 1 || rank > p || !(eps_prior > 0)) return GBFWI_EINVAL;
     GB_TRY(gb_check_local(X, V, lambda, std_out));
     cudaStream_t s = (cudaStream_t)stream;
-    const long long n = h->n;
-    const float *Xd;
+    const long long n = h->n, ld = h->ld;
+    const int k = h->k;
+    // the probe block in a store buffer (aligned rows for the tensor cores)
     if (X) {
-        GB_TRY(stage_in(h->X, X, (size_t)p * n, s, &Xd));
+        GB_TRY(stage_rows(h, h->X, X, p, s));
     } else {
-        GB_TRY(h->X.ensure((size_t)p * n * sizeof(float)));
-        philox_normal_kernel<<<grid_n((p * n + 3) / 4), 256, 0, s>>>(h->X.as<float>(), (long long)p * n, seed);
+        GB_TRY(h->X.ensure((size_t)p * ld * sizeof(float)));
+        philox_normal_kernel<<<grid_n((p * n + 3) / 4), 256, 0, s>>>(h->X.as<float>(), (long long)p * n, n, ld, seed);
         GB_LAUNCHED();
-        Xd = h->X.as<float>();
     }
-    GB_TRY(h->E.ensure((size_t)p * n * sizeof(float)));
-    GB_TRY(h->Q.ensure((size_t)p * n * sizeof(float)));
-    GB_TRY(reserve(h, p, true));
+    const float *Xd = h->X.as<float>();
+    GB_TRY(h->E.ensure((size_t)p * ld * sizeof(float)));
+    GB_TRY(h->Q.ensure((size_t)p * ld * sizeof(float)));
+    GB_TRY(h->V.ensure((size_t)p * ld * sizeof(float)));
+    GB_TRY(reserve(h, p, true, {{2 * k, p}, {p, p}, {p, 2 * p}}));
     float *E = h->E.as<float>(), *Q = h->Q.as<float>();
     // 1. E = (B_{n+1} - B0) X
-    // (coefficients S^T X, (B0 Y)^T X with compensated sums: E feeds the eigenvectors)
-    GB_TRY(apply_dev(h, Xd, p, E, 1.0, 1, s, true));
+    GB_TRY(apply_dev(h, Xd, ld, p, E, ld, 1.0, 1, s));
     // 2. rank-revealing basis of E: pivoted Cholesky of its FP64 Gram matrix,
     //    rows kept while their residual norm is >= 1e-4 of the largest (what an
     //    FP32 block resolves)
     const size_t pp = (size_t)p * p;
     double *G = h->small.as<double>() + small_apply_doubles(h, p);
-    double *A = G + pp, *R2 = A + pp, *Rinv = R2 + pp, *QE = Rinv + pp, *QX = QE + pp;
-    double *work = QX + pp;               // 4 pp + 4 p
+    double *A = G + pp, *R2 = A + pp, *Rinv = R2 + pp, *QEX = Rinv + pp;   // QEX: [p][2p]
+    double *work = QEX + 2 * pp;          // 4 pp + 4 p
     double *lam = work + 4 * pp + 4 * (size_t)p;
     int *rdev = reinterpret_cast<int *>(lam + p + 2);
     float *coef = h->coef.as<float>();
@@ -1063,48 +1080,52 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
         GB_CUDA(cudaFuncSetAttribute(gram_pivchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
         GB_CUDA(cudaFuncSetAttribute(omega_ls_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
     }
-    GB_TRY(atb(h, E, n, p, E, n, p, nullptr, G, p, s, true));
+    GB_TRY(atb(h, E, nullptr, p, p, E, nullptr, p, p, G, p, s));
     gram_pivchol_kernel<<<1, 512, use_smem ? ws : 0, s>>>(G, p, 1e-4, work, coef, rdev, flag, use_smem);
     GB_LAUNCHED();
     int r = 0;
     GB_CUDA(cudaMemcpyAsync(&r, rdev, sizeof(int), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     if (r < 1) return gb_nonfinite("probe block E = (B - B0) X is zero or not finite");
-    GB_TRY(combine(h, E, nullptr, p, p, coef, r, Q, nullptr, nullptr, 0.f, s));   // Q1 [r][n] in Q
+    GB_TRY(combine(h, E, nullptr, p, p, coef, r, Q, ld, nullptr, nullptr, 0, 0.f, s));   // Q1 [r] rows in Q
     // shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa
     // 2020): Q1 is orthonormal only up to its FP32 rounding times cond(R11),
     // and its FP32 Gram matrix may then miss definiteness; the first pass
     // adds 1e-5 tr(G) to the diagonal (well above the Gram's rounding), the
     // two unshifted passes make the rows orthonormal to FP32 rounding
-    GB_TRY(h->V.ensure((size_t)p * n * sizeof(float)));
     float *Qf = h->V.as<float>();
+    const size_t wc = (size_t)2 * r * r * sizeof(float);
+    const int chol_smem = wc <= 200 * 1024;
+    if (chol_smem) GB_CUDA(cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wc));
     for (int pass = 0; pass < 3; ++pass) {
-        GB_TRY(atb(h, Q, n, r, Q, n, r, nullptr, G, r, s));
-        chol_kernel<<<1, 256, 0, s>>>(G, r, pass == 0 ? 1e-5 : 0.0, A, R2, Rinv, coef, flag);
+        GB_TRY(atb(h, Q, nullptr, r, r, Q, nullptr, r, r, G, r, s));
+        chol_kernel<<<1, 512, chol_smem ? wc : 0, s>>>(G, r, pass == 0 ? 1e-5 : 0.0, reinterpret_cast<float *>(A),
+                                                       reinterpret_cast<float *>(Rinv), coef, flag, chol_smem);
         GB_LAUNCHED();
-        GB_TRY(combine(h, Q, nullptr, r, r, coef, r, Qf, nullptr, nullptr, 0.f, s));
+        GB_TRY(combine(h, Q, nullptr, r, r, coef, r, Qf, ld, nullptr, nullptr, 0, 0.f, s));
         std::swap(Q, Qf);                 // Q: current basis; Qf: free
     }
     std::swap(Q, Qf);                     // Qf: the basis; Q: free
-    // 3. Q^T E, Q^T X ; Omega by least squares ; eigenpairs
-    GB_TRY(atb(h, Qf, n, r, E, n, p, nullptr, QE, p, s, true));
-    // Q^T X compensated too: Omega = (Q^T E)(Q^T X)^-1 amplifies its error by cond(Q^T X)
-    GB_TRY(atb(h, Qf, n, r, Xd, n, p, nullptr, QX, p, s, true));
-    omega_ls_kernel<<<1, 512, use_smem ? ws : 0, s>>>(QE, QX, r, p, rank, work, lam, coef, flag, use_smem);
+    // 3. [Q^T E, Q^T X] in one pass over Q (Omega = (Q^T E)(Q^T X)^-1
+    //    amplifies their error by cond(Q^T X)); Omega by least squares; eigenpairs
+    GB_TRY(atb(h, Qf, nullptr, r, r, E, Xd, p, 2 * p, QEX, 2 * p, s));
+    omega_ls_kernel<<<1, 512, use_smem ? ws : 0, s>>>(QEX, QEX + p, 2 * p, r, p, rank, work, lam, coef, flag,
+                                                      use_smem);
     GB_LAUNCHED();
     // 4. V = Q U (first `rank` eigenvectors; rows beyond r are zero)
     const bool devV = V && gb_is_device_ptr(V);
-    float *Vd = devV ? V : E;     // E buffer is free now
-    GB_TRY(combine(h, Qf, nullptr, r, r, coef, rank, Vd, nullptr, nullptr, 0.f, s));
+    float *Vd = devV ? V : E;             // E buffer is free now
+    const long long ldv = devV ? n : ld;
+    GB_TRY(combine(h, Qf, nullptr, r, r, coef, rank, Vd, ldv, nullptr, nullptr, 0, 0.f, s));
     // 5. posterior std (Eq. 14)
     if (std_out) {
         bool devS = gb_is_device_ptr(std_out);
         float *Sd = devS ? std_out : Q;   // Q buffer is free now
-        std_kernel<<<grid_n(n), 256, 0, s>>>(Vd, lam, rank, h->B0.as<float>(), n, (float)eps_prior, Sd);
+        std_kernel<<<grid_n(n), 256, 0, s>>>(Vd, ldv, lam, rank, h->B0.as<float>(), n, (float)eps_prior, Sd);
         GB_LAUNCHED();
         if (!devS) GB_CUDA(cudaMemcpyAsync(std_out, Sd, n * sizeof(float), cudaMemcpyDeviceToHost, s));
     }
-    if (V && !devV) GB_CUDA(cudaMemcpyAsync(V, Vd, (size_t)rank * n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (V && !devV) GB_TRY(unstage_rows(h, V, Vd, rank, s));
     if (lambda)
         GB_CUDA(cudaMemcpyAsync(lambda, lam, rank * sizeof(double),
                                 gb_is_device_ptr(lambda) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
@@ -1129,13 +1150,13 @@ extern "C" int gbfwi_lowrank_exact(gbfwi_bfgs *h, int rank, double eps_prior, fl
     const int m = 2 * k;
     if (rank < 1 || rank > m) return GBFWI_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    const long long n = h->n;
+    const long long n = h->n, ld = h->ld;
     const size_t mm = (size_t)m * m;
-    GB_TRY(reserve(h, m, true));
+    GB_TRY(reserve(h, m, true, {{m, m}}));
     GB_TRY(h->ex.ensure((12 * mm + 4 * (size_t)m + 64) * sizeof(double)));
-    GB_TRY(h->E.ensure((size_t)m * n * sizeof(float)));
-    GB_TRY(h->Q.ensure((size_t)m * n * sizeof(float)));
-    GB_TRY(h->V.ensure((size_t)m * n * sizeof(float)));
+    GB_TRY(h->E.ensure((size_t)m * ld * sizeof(float)));
+    GB_TRY(h->Q.ensure((size_t)m * ld * sizeof(float)));
+    GB_TRY(h->V.ensure((size_t)m * ld * sizeof(float)));
     double *G = h->ex.as<double>();
     double *work = G + mm;                 // 4 mm
     double *C = work + 4 * mm, *M = C + mm, *P = M + mm, *T = P + mm;
@@ -1148,12 +1169,9 @@ extern "C" int gbfwi_lowrank_exact(gbfwi_bfgs *h, int rank, double eps_prior, fl
     GB_CUDA(cudaMemsetAsync(flag, 0, 16, s));
 
     // 1. rank-revealing basis of W = [S, B0 Y] (rows s_i, B0 y_i): pivoted
-    //    Cholesky of the column-scaled, compensated-sum Gram matrix, then
-    //    shifted CholeskyQR3
-    GB_TRY(atb(h, S, n, k, S, n, k, nullptr, G, m, s, true));
-    GB_TRY(atb(h, S, n, k, BY, n, k, nullptr, G + k, m, s, true));
-    GB_TRY(atb(h, BY, n, k, S, n, k, nullptr, G + (size_t)k * m, m, s, true));
-    GB_TRY(atb(h, BY, n, k, BY, n, k, nullptr, G + (size_t)k * m + k, m, s, true));
+    //    Cholesky of the column-scaled Gram matrix W^T W (one tensor-core
+    //    pass over S and B0 Y), then shifted CholeskyQR3
+    GB_TRY(atb(h, S, BY, k, m, S, BY, k, m, G, m, s));
     gram_scale_kernel<<<1, 256, 0, s>>>(G, m, d);
     GB_LAUNCHED();
     const size_t ws = (3 * mm + (size_t)m) * sizeof(double);
@@ -1169,18 +1187,21 @@ extern "C" int gbfwi_lowrank_exact(gbfwi_bfgs *h, int rank, double eps_prior, fl
     coef_colscale_kernel<<<grid_n((long long)r * m), 256, 0, s>>>(coef, r, m, d);
     GB_LAUNCHED();
     float *Qa = h->E.as<float>(), *Qb = h->Q.as<float>();
-    GB_TRY(combine(h, S, BY, k, m, coef, r, Qa, nullptr, nullptr, 0.f, s));
+    GB_TRY(combine(h, S, BY, k, m, coef, r, Qa, ld, nullptr, nullptr, 0, 0.f, s));
+    const size_t wc = (size_t)2 * r * r * sizeof(float);
+    const int chol_smem = wc <= 200 * 1024;
+    if (chol_smem) GB_CUDA(cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wc));
     for (int pass = 0; pass < 3; ++pass) {   // shifted CholeskyQR3, as in gbfwi_lowrank_invhess
-        GB_TRY(atb(h, Qa, n, r, Qa, n, r, nullptr, G, r, s));
-        chol_kernel<<<1, 256, 0, s>>>(G, r, pass == 0 ? 1e-5 : 0.0, cA, cR, cRi, coef, flag);
+        GB_TRY(atb(h, Qa, nullptr, r, r, Qa, nullptr, r, r, G, r, s));
+        chol_kernel<<<1, 512, chol_smem ? wc : 0, s>>>(G, r, pass == 0 ? 1e-5 : 0.0, reinterpret_cast<float *>(cA),
+                                                       reinterpret_cast<float *>(cRi), coef, flag, chol_smem);
         GB_LAUNCHED();
-        GB_TRY(combine(h, Qa, nullptr, r, r, coef, r, Qb, nullptr, nullptr, 0.f, s));
+        GB_TRY(combine(h, Qa, nullptr, r, r, coef, r, Qb, ld, nullptr, nullptr, 0, 0.f, s));
         std::swap(Qa, Qb);                 // Qa: current basis
     }
-    // 2. C = Q^T W and the middle matrix M of the compact form (gamma = 1):
-    //    B - B0 = W M W^T, M = [[R^-T (D + Y^T B0 Y) R^-1, -R^-T], [-R^-1, 0]]
-    GB_TRY(atb(h, Qa, n, r, S, n, k, nullptr, C, m, s, true));
-    GB_TRY(atb(h, Qa, n, r, BY, n, k, nullptr, C + k, m, s, true));
+    // 2. C = Q^T W (one pass) and the middle matrix M of the compact form
+    //    (gamma = 1): B - B0 = W M W^T, M = [[R^-T (D + Y^T B0 Y) R^-1, -R^-T], [-R^-1, 0]]
+    GB_TRY(atb(h, Qa, nullptr, r, r, S, BY, k, m, C, m, s));
     std::vector<double> Mh(mm, 0.0), Ri((size_t)k * k, 0.0);
     {
         const int km = h->kmax;
@@ -1213,7 +1234,7 @@ extern "C" int gbfwi_lowrank_exact(gbfwi_bfgs *h, int rank, double eps_prior, fl
     // 3. T = C M C^T, its eigenpairs, V = Q U
     exact_t_kernel<<<1, 512, 0, s>>>(C, M, r, m, P, T);
     GB_LAUNCHED();
-    const size_t we = ((size_t)r * r + r + 8) * sizeof(double);
+    const size_t we = ((size_t)r * r + r + 16 + ((size_t)r + 2) * (r + 2) / 4) * sizeof(double);
     const int use_smem2 = we <= 200 * 1024;
     if (use_smem2)
         GB_CUDA(cudaFuncSetAttribute(eig_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)we));
@@ -1221,15 +1242,16 @@ extern "C" int gbfwi_lowrank_exact(gbfwi_bfgs *h, int rank, double eps_prior, fl
     GB_LAUNCHED();
     const bool devV = V && gb_is_device_ptr(V);
     float *Vd = devV ? V : Qb;            // Qb is free
-    GB_TRY(combine(h, Qa, nullptr, r, r, coef, rank, Vd, nullptr, nullptr, 0.f, s));
+    const long long ldv = devV ? n : ld;
+    GB_TRY(combine(h, Qa, nullptr, r, r, coef, rank, Vd, ldv, nullptr, nullptr, 0, 0.f, s));
     if (std_out) {
         const bool devS = gb_is_device_ptr(std_out);
         float *Sd = devS ? std_out : h->V.as<float>();
-        std_kernel<<<grid_n(n), 256, 0, s>>>(Vd, lam, rank, h->B0.as<float>(), n, (float)eps_prior, Sd);
+        std_kernel<<<grid_n(n), 256, 0, s>>>(Vd, ldv, lam, rank, h->B0.as<float>(), n, (float)eps_prior, Sd);
         GB_LAUNCHED();
         if (!devS) GB_CUDA(cudaMemcpyAsync(std_out, Sd, n * sizeof(float), cudaMemcpyDeviceToHost, s));
     }
-    if (V && !devV) GB_CUDA(cudaMemcpyAsync(V, Vd, (size_t)rank * n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (V && !devV) GB_TRY(unstage_rows(h, V, Vd, rank, s));
     if (lambda)
         GB_CUDA(cudaMemcpyAsync(lambda, lam, rank * sizeof(double),
                                 gb_is_device_ptr(lambda) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));

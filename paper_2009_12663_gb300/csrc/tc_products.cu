@@ -4,16 +4,21 @@
 // Hessian (Section 2.3, Eq. 9, Algorithms 2-3; Byrd, Nocedal & Schnabel
 // 1994), and the Gram / projection products of Algorithm 3.
 //
-// Precision.  Every operand is FP32.  Each value x is split into two TF32
-// parts, hi = tf32(x) and lo = tf32(x - hi), and a product is taken as
-// hi*hi + hi*lo + lo*hi on the tensor cores (mma.sync m16n8k8 TF32, FP32
-// accumulation): the 3xTF32 scheme of Ootomo & Yokota (2022), whose error
-// is that of an FP32 product (the dropped lo*lo term and the residual of lo
-// are ~2^-22 relative).  The long sums over n of the split-K products are
-// accumulated per split in a compensated FP32 pair (TwoSum of Knuth, taken
-// after every 32 products of a K step), so they are close to an exact sum
-// of the FP32 products, and the splits are reduced in FP64.  The row
-// combinations sum at most 128 terms and keep a plain FP32 accumulator.
+// Precision.  Every operand is FP32.  Each value x is split exactly into
+// three bfloat16 parts, x = x1 + x2 + x3 (x1 = bf16(x), x2 = bf16(x - x1),
+// x3 = x - x1 - x2: 8 significant bits each, 24 in all), and a product is
+// taken as the six terms x_i y_j with i + j <= 4 on the tensor cores
+// (mma.sync m16n8k16 BF16, products exact in the FP32 accumulator), small
+// terms first; the dropped x2 y3, x3 y2, x3 y3 are below 2^-23 of |x y|, so a
+// product is as accurate as an FP32 product (the splitting of Ootomo &
+// Yokota (2022) carried to three bfloat16 parts, which is exact where two
+// TF32 parts are not).  The tensor core's FP32 accumulation is kept short:
+// after every 16-deep K step its sum is folded into a compensated FP32 pair
+// (TwoSum of Knuth), so the long sums over n of the split-K products are
+// close to exact sums of the FP32 products, and the splits are reduced in
+// FP64; the row combinations sum at most 128 terms the same way.  (A probe
+// of mma.sync on sm_103a: a BF16 or TF32 MMA keeps about 24 bits below its
+// largest term and truncates the rest.)
 //
 // Layout: rows are vectors of length n with a row stride ld (a multiple of
 // 4 floats, rows 16-byte aligned); both kernels stage their operands in
@@ -26,26 +31,46 @@
 
 namespace {
 
-__device__ __forceinline__ unsigned tf32_of(float x)
+// two floats -> packed bfloat16 pair (round to nearest even), lo_col in the
+// lower half
+__device__ __forceinline__ unsigned pack_bf16(float lo_col, float hi_col)
 {
     unsigned r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi_col), "f"(lo_col));
     return r;
 }
 
-__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo)
+// exact three-part bfloat16 split of the pair (u, v): u = u1 + u2 + u3 with
+// the parts packed as (u_i, v_i) in p[i]
+__device__ __forceinline__ void split3(float u, float v, unsigned (&p)[3])
 {
-    hi = tf32_of(x);
-    lo = tf32_of(x - __uint_as_float(hi));
+    p[0] = pack_bf16(u, v);
+    const float ur = __fsub_rn(u, __uint_as_float(p[0] << 16));
+    const float vr = __fsub_rn(v, __uint_as_float(p[0] & 0xffff0000u));
+    p[1] = pack_bf16(ur, vr);
+    const float ur2 = __fsub_rn(ur, __uint_as_float(p[1] << 16));
+    const float vr2 = __fsub_rn(vr, __uint_as_float(p[1] & 0xffff0000u));
+    p[2] = pack_bf16(ur2, vr2);
 }
 
-__device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
                                          unsigned b0, unsigned b1)
 {
-    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
                  "{%0,%1,%2,%3};\n"
                  : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
                  : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// d += the six terms a_i b_j, i + j <= 4 (parts 0..2), smallest first
+__device__ __forceinline__ void mma_split6(float (&d)[4], const unsigned (&a)[3][4], const unsigned (&b)[3][2])
+{
+    mma_bf16(d, a[2][0], a[2][1], a[2][2], a[2][3], b[0][0], b[0][1]);
+    mma_bf16(d, a[0][0], a[0][1], a[0][2], a[0][3], b[2][0], b[2][1]);
+    mma_bf16(d, a[1][0], a[1][1], a[1][2], a[1][3], b[1][0], b[1][1]);
+    mma_bf16(d, a[1][0], a[1][1], a[1][2], a[1][3], b[0][0], b[0][1]);
+    mma_bf16(d, a[0][0], a[0][1], a[0][2], a[0][3], b[1][0], b[1][1]);
+    mma_bf16(d, a[0][0], a[0][1], a[0][2], a[0][3], b[0][0], b[0][1]);
 }
 
 __device__ __forceinline__ void cp16(void *smem, const void *gmem, int src_bytes)
@@ -76,22 +101,29 @@ __device__ __forceinline__ const float *row_of(const float *P1, const float *P2,
 // ---------------------------------------------------------------------------
 // split-K product: part[sx][a][b] = sum_{i in split sx} A_a[i] B_b[i]
 // CTA: 64 x 64 output tile, 4 warps of 32 x 32 (2 m16 x 4 n8 MMA tiles);
-// K staged 32 at a time, three-stage cp.async pipeline.
+// K staged 32 at a time (two 16-deep MMA steps) through a double-buffered
+// cp.async pipeline; every staged element is split into its three bfloat16
+// parts once, into shared planes the fragments are read from.
 // grid (ceil(kb / 64), ceil(ka / 64), nsplit): the splits vary slowest, so
 // the tiles that read the same K range run together and share it in L2.
 // ---------------------------------------------------------------------------
 
-constexpr int AT_M = 64, AT_N = 64, AT_K = 32, AT_P = AT_K + 4, AT_STAGES = 3, AT_THREADS = 128;
-constexpr size_t AT_SMEM = (size_t)AT_STAGES * (AT_M + AT_N) * AT_P * sizeof(float);
+// row pitches: raw FP32 tiles 32 floats (16-byte cp.async rows), split
+// planes 20 words (the fragment loads of a warp hit 32 distinct banks)
+constexpr int AT_M = 64, AT_N = 64, AT_K = 32, AT_P = AT_K, AT_PP = AT_K / 2 + 4, AT_THREADS = 128;
+constexpr size_t AT_RAW = (size_t)(AT_M + AT_N) * AT_P;          // floats of one raw stage
+constexpr size_t AT_PLANE = (size_t)(AT_M + AT_N) * AT_PP;       // words of one split plane
+constexpr size_t AT_SMEM = (2 * AT_RAW + 3 * AT_PLANE) * sizeof(float);
 
-__global__ void __launch_bounds__(AT_THREADS) atb_tc_kernel(const float *__restrict__ A1, const float *__restrict__ A2,
+__global__ void __launch_bounds__(AT_THREADS, 3) atb_tc_kernel(const float *__restrict__ A1, const float *__restrict__ A2,
                                                             int ka1, int ka, const float *__restrict__ B1,
                                                             const float *__restrict__ B2, int kb1, int kb,
                                                             long long ld, long long n, long long chunk,
                                                             double *__restrict__ part)
 {
     extern __shared__ float4 at_smem4[];
-    float *sm = reinterpret_cast<float *>(at_smem4);
+    float *raw = reinterpret_cast<float *>(at_smem4);                  // [2][128 rows][32]
+    unsigned *pl = reinterpret_cast<unsigned *>(raw + 2 * AT_RAW);     // [3][128 rows][20]
     const int sx = blockIdx.z;
     const int a0 = blockIdx.y * AT_M, b0 = blockIdx.x * AT_N;
     const long long ib = (long long)sx * chunk;
@@ -101,18 +133,16 @@ __global__ void __launch_bounds__(AT_THREADS) atb_tc_kernel(const float *__restr
     const int g = lane >> 2, t = lane & 3;
     const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
 
-    // stage loader: 64 rows of A and 64 rows of B, 32 floats each = 8
-    // 16-byte chunks per row; 1024 chunks, 8 per thread
-    auto load = [&](int stage, int kt) {
-        float *As = sm + (size_t)stage * (AT_M + AT_N) * AT_P;
-        float *Bs = As + AT_M * AT_P;
+    // raw stage: rows 0..63 of A then 0..63 of B, 8 16-byte chunks each
+    auto load = [&](int buf, int kt) {
+        float *dst = raw + (size_t)buf * AT_RAW;
         const long long i0 = ib + (long long)kt * AT_K;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int q = tid + u * AT_THREADS;           // 0..1023
-            const int r = (q >> 3) & 63, c = q & 7;
-            const bool isb = q >= 512;
-            const int row = (isb ? b0 : a0) + r;
+            const int r = q >> 3, c = q & 7;               // r: 0..127
+            const bool isb = r >= 64;
+            const int row = (isb ? b0 - 64 : a0) + r;
             const int lim = isb ? kb : ka;
             const long long i = i0 + 4 * c;
             int bytes = 0;
@@ -121,7 +151,7 @@ __global__ void __launch_bounds__(AT_THREADS) atb_tc_kernel(const float *__restr
                 src = isb ? row_of(B1, B2, kb1, row, ld) + i : row_of(A1, A2, ka1, row, ld) + i;
                 bytes = (int)min(16LL, (ie - i) * 4);
             }
-            cp16((isb ? Bs : As) + r * AT_P + 4 * c, src, bytes);
+            cp16(dst + r * AT_P + 4 * c, src, bytes);
         }
     };
 
@@ -139,51 +169,60 @@ __global__ void __launch_bounds__(AT_THREADS) atb_tc_kernel(const float *__restr
     cp_commit();
     for (int kt = 0; kt < nk; ++kt) {
         cp_wait<1>();
-        __syncthreads();
-        if (kt + 2 < nk) load((kt + 2) % AT_STAGES, kt + 2);
+        __syncthreads();                                   // raw stage kt landed; planes free
+        {
+            // split every element of the stage once: 128 rows x 16 pairs
+            const float *src = raw + (size_t)(kt & 1) * AT_RAW;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int q = tid + u * AT_THREADS;        // 0..2047
+                const int r = q >> 4, c = q & 15;
+                const float2 v = *reinterpret_cast<const float2 *>(src + r * AT_P + 2 * c);
+                unsigned s3[3];
+                split3(v.x, v.y, s3);
+#pragma unroll
+                for (int part = 0; part < 3; ++part) pl[part * AT_PLANE + r * AT_PP + c] = s3[part];
+            }
+        }
+        __syncthreads();                                   // planes ready; raw stage kt free
+        if (kt + 2 < nk) load(kt & 1, kt + 2);
         cp_commit();
-        const float *As = sm + (size_t)(kt % AT_STAGES) * (AT_M + AT_N) * AT_P;
-        const float *Bs = As + AT_M * AT_P;
-        float D[2][4][4];
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
+        for (int kk = 0; kk < AT_K; kk += 16) {
+            unsigned a[2][3][4], b[4][3][2];
+            const int kw = kk / 2 + t;                     // word of the pair (kk + 2t, kk + 2t + 1)
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
+            for (int part = 0; part < 3; ++part) {
+                const unsigned *P = pl + part * AT_PLANE;
 #pragma unroll
-                for (int v = 0; v < 4; ++v) D[mt][nt][v] = 0.f;
+                for (int mt = 0; mt < 2; ++mt) {
+                    const int r = wm + mt * 16 + g;
+                    a[mt][part][0] = P[r * AT_PP + kw];
+                    a[mt][part][1] = P[(r + 8) * AT_PP + kw];
+                    a[mt][part][2] = P[r * AT_PP + kw + 4];
+                    a[mt][part][3] = P[(r + 8) * AT_PP + kw + 4];
+                }
 #pragma unroll
-        for (int kk = 0; kk < AT_K; kk += 8) {
-            unsigned ah[2][4], al[2][4], bh[4][2], bl[4][2];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const float *p = As + (wm + mt * 16 + g) * AT_P + kk + t;
-                split_tf32(p[0], ah[mt][0], al[mt][0]);
-                split_tf32(p[8 * AT_P], ah[mt][1], al[mt][1]);
-                split_tf32(p[4], ah[mt][2], al[mt][2]);
-                split_tf32(p[8 * AT_P + 4], ah[mt][3], al[mt][3]);
+                for (int nt = 0; nt < 4; ++nt) {
+                    const int r = 64 + wn + nt * 8 + g;
+                    b[nt][part][0] = P[r * AT_PP + kw];
+                    b[nt][part][1] = P[r * AT_PP + kw + 4];
+                }
             }
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const float *p = Bs + (wn + nt * 8 + g) * AT_P + kk + t;
-                split_tf32(p[0], bh[nt][0], bl[nt][0]);
-                split_tf32(p[4], bh[nt][1], bl[nt][1]);
-            }
+            // each 16-product sum goes into the compensated pair at once:
+            // the tensor core truncates its FP32 sums, and a longer run in
+            // its accumulator measurably biases the small directions of an
+            // ill-conditioned block
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
                 for (int nt = 0; nt < 4; ++nt) {
-                    mma_tf32(D[mt][nt], al[mt][0], al[mt][1], al[mt][2], al[mt][3], bh[nt][0], bh[nt][1]);
-                    mma_tf32(D[mt][nt], ah[mt][0], ah[mt][1], ah[mt][2], ah[mt][3], bl[nt][0], bl[nt][1]);
-                    mma_tf32(D[mt][nt], ah[mt][0], ah[mt][1], ah[mt][2], ah[mt][3], bh[nt][0], bh[nt][1]);
+                    float D[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma_split6(D, a[mt], b[nt]);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) two_sum_add(S[mt][nt][v], E[mt][nt][v], D[v]);
                 }
         }
-        // fold this K step's 32-product sums into the compensated pairs
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) two_sum_add(S[mt][nt][v], E[mt][nt][v], D[mt][nt][v]);
     }
     cp_wait<0>();
 #pragma unroll
@@ -213,13 +252,22 @@ __global__ void split_reduce_kernel(const double *__restrict__ part, int nsplit,
 // ---------------------------------------------------------------------------
 // row combination: out[c][i] = sum_a coef[c][a] R_a[i] + beta dw[i] Xc[c][i]
 // for c in [c0, c0 + 16 MT) (blockIdx.y selects c0 = 64 blockIdx.y).
-// coef (FP32, [nc][ktot]) stays in shared memory; persistent CTAs walk over
-// 64-column tiles, streaming R in K steps of 32 rows through a four-stage
-// cp.async pipeline.  4 warps, each all MT m16 tiles x 2 n8 tiles (16
-// columns).
+// coef stays in shared memory, split once; persistent CTAs walk over
+// 64-column tiles, streaming R in K steps of 32 rows (two 16-deep MMA steps)
+// through a four-stage cp.async pipeline.  4 warps, each all MT m16 tiles x
+// 2 n8 tiles (16 columns).  The sums over K (at most 128 terms) are folded
+// into compensated FP32 pairs after every 16-deep step, as in the split-K
+// product: the basis combinations of the randomized SVD have ill-conditioned
+// coefficients, and a plain FP32 sum of their terms loses the small
+// directions.
 // ---------------------------------------------------------------------------
 
-constexpr int CB_N = 64, CB_K = 32, CB_RP = CB_N + 8, CB_STAGES = 4, CB_THREADS = 128;
+// R stages are raw FP32 [32 rows][64 columns]; each stage is split once into
+// three planes of row pairs [16][72 words] (conflict-free fragment loads);
+// coef is split once into three planes [16 MT][K/2 + 4 words].
+constexpr int CB_N = 64, CB_K = 32, CB_RPP = CB_N + 8, CB_STAGES = 4, CB_THREADS = 128;
+constexpr size_t CB_RAW = (size_t)CB_K * CB_N;            // floats of one raw stage
+constexpr size_t CB_PLANE = (size_t)(CB_K / 2) * CB_RPP;  // words of one split plane of R
 
 template <int MT>
 __global__ void __launch_bounds__(CB_THREADS) combine_tc_kernel(const float *__restrict__ R1,
@@ -231,28 +279,35 @@ __global__ void __launch_bounds__(CB_THREADS) combine_tc_kernel(const float *__r
                                                                 float beta)
 {
     extern __shared__ float4 cb_smem4[];
-    float *sm = reinterpret_cast<float *>(cb_smem4);
     const int kp = (ktot + CB_K - 1) / CB_K * CB_K;      // K padded to whole steps
-    const int cpitch = kp + 4;
-    float *Cs = sm;                                      // [16 MT][cpitch]
-    float *Rs = sm + 16 * MT * cpitch;                   // [stages][CB_K][CB_RP]
+    const int cpp = kp / 2 + 4;                          // coef plane pitch in words
+    float *raw = reinterpret_cast<float *>(cb_smem4);                   // [stages][32][64]
+    unsigned *rp = reinterpret_cast<unsigned *>(raw + CB_STAGES * CB_RAW);   // [3][16][72]
+    unsigned *cp = rp + 3 * CB_PLANE;                                   // [3][16 MT][cpp]
     const int c0 = blockIdx.y * 64;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
     const int wn = warp * 16;
-    for (int q = tid; q < 16 * MT * cpitch; q += CB_THREADS) {
-        const int c = q / cpitch, a = q - c * cpitch;
-        Cs[q] = (c0 + c < nc && a < ktot) ? coef[(long long)(c0 + c) * ktot + a] : 0.f;
+    // coef planes: pairs along K of each output row
+    for (int q = tid; q < 16 * MT * (kp / 2); q += CB_THREADS) {
+        const int c = q / (kp / 2), w = q - c * (kp / 2);
+        const int a = 2 * w;
+        const bool ok = c0 + c < nc;
+        const float u = (ok && a < ktot) ? coef[(long long)(c0 + c) * ktot + a] : 0.f;
+        const float v = (ok && a + 1 < ktot) ? coef[(long long)(c0 + c) * ktot + a + 1] : 0.f;
+        unsigned s3[3];
+        split3(u, v, s3);
+#pragma unroll
+        for (int part = 0; part < 3; ++part) cp[(size_t)part * 16 * MT * cpp + c * cpp + w] = s3[part];
     }
     const long long ntiles = (n + CB_N - 1) / CB_N;
     const int nks = kp / CB_K;
-    // flat sequence of (tile, K step) pairs of this CTA
     const long long my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const long long total = my_tiles * nks;
     auto load = [&](long long f) {
         const long long tile = blockIdx.x + (f / nks) * gridDim.x;
         const int ks = (int)(f % nks);
-        float *dst = Rs + (size_t)(f % CB_STAGES) * CB_K * CB_RP;
+        float *dst = raw + (size_t)(f % CB_STAGES) * CB_RAW;
         const long long i0 = tile * CB_N;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {                     // 32 rows x 16 chunks = 512 chunks
@@ -266,14 +321,14 @@ __global__ void __launch_bounds__(CB_THREADS) combine_tc_kernel(const float *__r
                 src = row_of(R1, R2, k1, a, ldr) + i;
                 bytes = (int)min(16LL, (n - i) * 4);
             }
-            cp16(dst + r * CB_RP + 4 * c, src, bytes);
+            cp16(dst + r * CB_N + 4 * c, src, bytes);
         }
     };
     for (long long f = 0; f < CB_STAGES - 1; ++f) {
         if (f < total) load(f);
         cp_commit();
     }
-    float D[MT][2][4];
+    float S[MT][2][4], E[MT][2][4];
     for (long long f = 0; f < total; ++f) {
         const int ks = (int)(f % nks);
         if (ks == 0) {
@@ -282,35 +337,54 @@ __global__ void __launch_bounds__(CB_THREADS) combine_tc_kernel(const float *__r
 #pragma unroll
                 for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) D[mt][nt][v] = 0.f;
+                    for (int v = 0; v < 4; ++v) S[mt][nt][v] = E[mt][nt][v] = 0.f;
         }
         cp_wait<CB_STAGES - 2>();
-        __syncthreads();
+        __syncthreads();                                   // raw stage f landed; R planes free
+        {
+            const float *src = raw + (size_t)(f % CB_STAGES) * CB_RAW;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {                  // 16 row pairs x 64 columns
+                const int q = tid + u * CB_THREADS;
+                const int j = q >> 6, c = q & 63;
+                unsigned s3[3];
+                split3(src[(2 * j) * CB_N + c], src[(2 * j + 1) * CB_N + c], s3);
+#pragma unroll
+                for (int part = 0; part < 3; ++part) rp[part * CB_PLANE + j * CB_RPP + c] = s3[part];
+            }
+        }
+        __syncthreads();                                   // R planes ready
         if (f + CB_STAGES - 1 < total) load(f + CB_STAGES - 1);
         cp_commit();
-        const float *Rb = Rs + (size_t)(f % CB_STAGES) * CB_K * CB_RP;
 #pragma unroll
-        for (int kk = 0; kk < CB_K; kk += 8) {
-            unsigned bh[2][2], bl[2][2];
+        for (int kk = 0; kk < CB_K; kk += 16) {
+            unsigned b[2][3][2];
 #pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-                const float *p = Rb + (kk + t) * CB_RP + wn + nt * 8 + g;
-                split_tf32(p[0], bh[nt][0], bl[nt][0]);
-                split_tf32(p[4 * CB_RP], bh[nt][1], bl[nt][1]);
-            }
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-                const float *p = Cs + (mt * 16 + g) * cpitch + ks * CB_K + kk + t;
-                unsigned ah0, al0, ah1, al1, ah2, al2, ah3, al3;
-                split_tf32(p[0], ah0, al0);
-                split_tf32(p[8 * cpitch], ah1, al1);
-                split_tf32(p[4], ah2, al2);
-                split_tf32(p[8 * cpitch + 4], ah3, al3);
+            for (int part = 0; part < 3; ++part)
 #pragma unroll
                 for (int nt = 0; nt < 2; ++nt) {
-                    mma_tf32(D[mt][nt], al0, al1, al2, al3, bh[nt][0], bh[nt][1]);
-                    mma_tf32(D[mt][nt], ah0, ah1, ah2, ah3, bl[nt][0], bl[nt][1]);
-                    mma_tf32(D[mt][nt], ah0, ah1, ah2, ah3, bh[nt][0], bh[nt][1]);
+                    const unsigned *P = rp + part * CB_PLANE + (kk / 2 + t) * CB_RPP + wn + nt * 8 + g;
+                    b[nt][part][0] = P[0];
+                    b[nt][part][1] = P[4 * CB_RPP];
+                }
+            const int kw = (ks * CB_K + kk) / 2 + t;
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                unsigned a[3][4];
+#pragma unroll
+                for (int part = 0; part < 3; ++part) {
+                    const unsigned *P = cp + (size_t)part * 16 * MT * cpp + (mt * 16 + g) * cpp + kw;
+                    a[part][0] = P[0];
+                    a[part][1] = P[8 * cpp];
+                    a[part][2] = P[4];
+                    a[part][3] = P[8 * cpp + 4];
+                }
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    float D[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma_split6(D, a, b[nt]);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) two_sum_add(S[mt][nt][v], E[mt][nt][v], D[v]);
                 }
             }
         }
@@ -325,7 +399,7 @@ __global__ void __launch_bounds__(CB_THREADS) combine_tc_kernel(const float *__r
                         const int c = c0 + mt * 16 + g + ((v & 2) ? 8 : 0);
                         const long long i = i0 + wn + nt * 8 + 2 * t + (v & 1);
                         if (c < nc && i < n) {
-                            float r = D[mt][nt][v];
+                            float r = S[mt][nt][v] + E[mt][nt][v];
                             if (beta != 0.f) r = fmaf(beta * dw[i], Xc[(long long)c * ldx + i], r);
                             out[(long long)c * ldo + i] = r;
                         }
@@ -340,16 +414,18 @@ int launch_combine(const float *R1, const float *R2, int k1, int ktot, long long
                    long long n, float *out, long long ldo, const float *dw, const float *Xc, long long ldx,
                    float beta, cudaStream_t s)
 {
+    auto bytes_for = [](int kp) {
+        return (CB_STAGES * CB_RAW + 3 * CB_PLANE + (size_t)3 * 16 * MT * (kp / 2 + 4)) * sizeof(float);
+    };
     const int kp = (ktot + CB_K - 1) / CB_K * CB_K;
-    const size_t smem = ((size_t)16 * MT * (kp + 4) + (size_t)CB_STAGES * CB_K * CB_RP) * sizeof(float);
-    const size_t smem_max = ((size_t)16 * MT * (128 + 4) + (size_t)CB_STAGES * CB_K * CB_RP) * sizeof(float);
+    const size_t smem = bytes_for(kp);
     static bool attr[64] = {};
     int dev = 0;
     GB_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return GBFWI_EINVAL;
     if (!attr[dev]) {
         GB_CUDA(cudaFuncSetAttribute(combine_tc_kernel<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_max));
+                                     (int)bytes_for(128)));
         attr[dev] = true;
     }
     int nsm = 152, occ = 1;

@@ -93,7 +93,11 @@ def test_host_arrays_accepted():
 
 
 def _align(V, Vr):
-    """Cosines between matching eigenvectors (sign-free)."""
+    """Cosines between matching eigenvectors (sign-free), in FP64: with the
+    norms of FP32 rows taken in FP32, sqrt(1 - cos^2) would carry ~3e-4 of
+    rounding noise."""
+    V = np.asarray(V, np.float64)
+    Vr = np.asarray(Vr, np.float64)
     return np.abs(np.sum(V * Vr, axis=1)) / (np.linalg.norm(V, axis=1) * np.linalg.norm(Vr, axis=1))
 
 

@@ -73,13 +73,14 @@ def test_misfit_noalloc_short_shots_after_long_ones():
     syn = torch.randn(4, long_n, device=DEV, generator=g)
     obs = torch.randn(4, long_n, device=DEV, generator=g)
     rc, out = _call(L, syn, obs, 4, long_n, dt)
-    ref = 0.5 * dt * ((syn.double() - obs.double()) ** 2).sum(1).cpu().numpy()
-    assert rc == 0 and np.allclose(out, ref, rtol=1e-12)
+    # the residual is formed in FP32 and squared and summed in FP64
+    ref = 0.5 * dt * ((syn - obs).double() ** 2).sum(1).cpu().numpy()
+    assert rc == 0 and np.allclose(out, ref, rtol=1e-9)
     s2, o2 = syn[:, :short_n].contiguous(), obs[:, :short_n].contiguous()
     for _ in range(2):
         rc, out = _call(L, s2, o2, 4, short_n, dt)
-        ref = 0.5 * dt * ((s2.double() - o2.double()) ** 2).sum(1).cpu().numpy()
-        assert rc == 0 and np.allclose(out, ref, rtol=1e-12), (out, ref)
+        ref = 0.5 * dt * ((s2 - o2).double() ** 2).sum(1).cpu().numpy()
+        assert rc == 0 and np.allclose(out, ref, rtol=1e-9), (out, ref)
 
 
 def test_misfit_noalloc_reserves_no_device_memory():
