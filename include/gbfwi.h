@@ -53,7 +53,7 @@ enum {
     GBFWI_ECFL = -4,        /* dt * vp_max / (min GLL node spacing) > 0.5 */
     GBFWI_ECURV = -5,       /* BFGS pair rejected: y^T s <= 1e-12 |s| |y| */
     GBFWI_ENONFINITE = -6,  /* a NaN or Inf reached the seismograms or the model */
-    GBFWI_ETIMEOUT = -7,    /* a bounded device-side wait gave up */
+    /* -7 is not used */
     GBFWI_ENOMODEL = -8,    /* simulation requested before gbfwi_set_model */
     GBFWI_ESCRATCH = -9     /* request larger than the fixed scratch of a no-allocation entry point */
 };
@@ -224,6 +224,19 @@ int gbfwi_bfgs_apply(gbfwi_bfgs *b, const float *X, int p, float *Z, double gamm
  * -> EINVAL, ECUDA, ENOMEM, ENONFINITE (E = 0 or non-finite, a singular
  *    Q^T X). */
 int gbfwi_lowrank_invhess(gbfwi_bfgs *b, const float *X, int p, int rank,
+                          unsigned long long seed, double eps_prior, float *V,
+                          double *lambda, float *std, void *stream);
+
+/* Two-pass variant of gbfwi_lowrank_invhess (Algorithm 3 with the
+ * Rayleigh-Ritz second pass of Halko, Martinsson & Tropp 2011, Alg. 5.3):
+ * the same probes, E = (B_{n+1} - B0) X and rank-revealing basis Q, then
+ * a second application of the compact form to the basis,
+ * C = Q (B_{n+1} - B0) Q^T (r x r, symmetrised), U Lambda U^T = C,
+ * V = U^T Q.  It avoids the (Q^T X)^-1 of the single pass, whose error
+ * grows with cond(Q^T X), for the cost of one more block apply (r rows).
+ * Arguments, outputs and errors as gbfwi_lowrank_invhess.  Synchronises
+ * the stream. */
+int gbfwi_lowrank_twopass(gbfwi_bfgs *b, const float *X, int p, int rank,
                           unsigned long long seed, double eps_prior, float *V,
                           double *lambda, float *std, void *stream);
 

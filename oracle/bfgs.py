@@ -102,6 +102,27 @@ def rsvd_single_pass(E: np.ndarray, X: np.ndarray, rank: int):
     return V[:rank], lam[:rank]
 
 
+def rsvd_two_pass(apply, X: np.ndarray, rank: int):
+    """Two-pass variant of Algorithm 3 (the Rayleigh-Ritz form of the
+    randomized eigendecomposition, Halko, Martinsson & Tropp 2011, Alg. 5.3):
+    the first pass E = A X gives the basis, QR = E; the second applies the
+    operator to the basis, C = Q^T A Q, and C = U Lambda U^T, V = Q U.  No
+    (Q^T X)^-1 appears, at the cost of a second application of A.
+    `apply(M)` returns A M for a block M of rows ([m][n] -> [m][n]).  C is
+    symmetrised; eigenpairs ordered by |lambda|, largest first; the first
+    `rank` are returned as V [rank][n], lam [rank]."""
+    E = np.asarray(apply(np.asarray(X, np.float64)), np.float64)
+    Q, _ = np.linalg.qr(E.T)                       # n x p, orthonormal columns
+    AQ = np.asarray(apply(Q.T), np.float64)        # rows: A q_j
+    C = Q.T @ AQ.T
+    C = 0.5 * (C + C.T)
+    lam, U = np.linalg.eigh(C)
+    order = np.argsort(-np.abs(lam), kind="stable")
+    lam, U = lam[order], U[:, order]
+    V = (Q @ U).T
+    return V[:rank], lam[:rank]
+
+
 def posterior_std(V: np.ndarray, lam: np.ndarray, B0: np.ndarray, eps: float = 1.0):
     """Eqs. 10 and 14 with C_m = eps I:  C_M = eps (V Lambda V^T + B0),
     std = sqrt(diag C_M); negative diagonals (from a truncated, indefinite

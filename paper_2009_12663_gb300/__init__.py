@@ -188,6 +188,12 @@ class Bfgs:
                                           float(eps_prior), ptr(V, F32), ptr(lam, F64), ptr(std, F32),
                                           stream_of(X, V, lam, std)), "lowrank_invhess")
 
+    def lowrank_twopass(self, p, rank, seed=0, eps_prior=1.0, X=None, V=None, lam=None, std=None):
+        """Algorithm 3 with the Rayleigh-Ritz second pass C = Q (B - B0) Q^T."""
+        check(lib().gbfwi_lowrank_twopass(self._h, ptr(X, F32), int(p), int(rank), int(seed),
+                                          float(eps_prior), ptr(V, F32), ptr(lam, F64), ptr(std, F32),
+                                          stream_of(X, V, lam, std)), "lowrank_twopass")
+
     def lowrank_exact(self, rank, eps_prior=1.0, V=None, lam=None, std=None):
         """Exact eigenpairs of B_{n+1} - B0 (rank <= 2k) from a QR of [S, B0 Y]."""
         check(lib().gbfwi_lowrank_exact(self._h, int(rank), float(eps_prior), ptr(V, F32), ptr(lam, F64),

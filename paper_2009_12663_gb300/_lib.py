@@ -19,7 +19,7 @@ from . import build as _build
 GBFWI_OK = 0
 ERRORS = {
     -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ECFL", -5: "ECURV",
-    -6: "ENONFINITE", -7: "ETIMEOUT", -8: "ENOMODEL", -9: "ESCRATCH",
+    -6: "ENONFINITE", -8: "ENOMODEL", -9: "ESCRATCH",
 }
 
 #: every symbol declared in include/gbfwi.h
@@ -28,7 +28,7 @@ ABI_SYMBOLS = (
     "gbfwi_num_tiles", "gbfwi_tile_shape", "gbfwi_get_schedule", "gbfwi_set_schedule",
     "gbfwi_set_model", "gbfwi_forward", "gbfwi_misfit", "gbfwi_adjoint_gradient", "gbfwi_precond_diag",
     "gbfwi_bfgs_create", "gbfwi_bfgs_update", "gbfwi_bfgs_count", "gbfwi_bfgs_apply",
-    "gbfwi_lowrank_invhess", "gbfwi_lowrank_exact", "gbfwi_bfgs_destroy", "gbfwi_launch_count", "gbfwi_enable_timing",
+    "gbfwi_lowrank_invhess", "gbfwi_lowrank_twopass", "gbfwi_lowrank_exact", "gbfwi_bfgs_destroy", "gbfwi_launch_count", "gbfwi_enable_timing",
     "gbfwi_last_phase_times", "gbfwi_misfit_noalloc", "gbfwi_strerror",
     "gbfwi_unet_create", "gbfwi_unet_destroy", "gbfwi_unet_num_params", "gbfwi_unet_layer_info",
     "gbfwi_unet_set_params", "gbfwi_unet_get_params", "gbfwi_unet_forward", "gbfwi_unet_gradient",
@@ -98,6 +98,8 @@ def lib(path: str | None = None):
         L.gbfwi_bfgs_count.argtypes = [vp]
         L.gbfwi_bfgs_apply.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_double, ctypes.c_int, vp]
         L.gbfwi_lowrank_invhess.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
+                                            ctypes.c_double, vp, vp, vp, vp]
+        L.gbfwi_lowrank_twopass.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
                                             ctypes.c_double, vp, vp, vp, vp]
         L.gbfwi_lowrank_exact.argtypes = [vp, ctypes.c_int, ctypes.c_double, vp, vp, vp, vp]
         L.gbfwi_bfgs_destroy.argtypes = [vp]

@@ -658,6 +658,18 @@ __global__ void coef_colscale_kernel(float *__restrict__ coef, int r, int m, con
         coef[q] = (float)((double)coef[q] * d[q % m]);
 }
 
+// T <- (T + T^T) / 2 in place, r x r, one CTA
+__global__ void sym_kernel(double *__restrict__ T, int r)
+{
+    for (int q = threadIdx.x; q < r * r; q += blockDim.x) {
+        const int i = q / r, j = q - i * r;
+        if (j <= i) continue;
+        const double v = 0.5 * (T[(long long)i * r + j] + T[(long long)j * r + i]);
+        T[(long long)i * r + j] = v;
+        T[(long long)j * r + i] = v;
+    }
+}
+
 // T = C M C^T (symmetrised), C [r][m], M [m][m] symmetric, FP64, one CTA;
 // P [r][m] scratch
 __global__ void exact_t_kernel(const double *__restrict__ C, const double *__restrict__ M, int r, int m,
@@ -1038,12 +1050,16 @@ extern "C" int gbfwi_bfgs_apply(gbfwi_bfgs *h, const float *X, int p, float *Z, 
     return GBFWI_OK;
 }
 
-extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int rank, unsigned long long seed,
-                                     double eps_prior, float *V, double *lambda, float *std_out, void *stream)
+namespace {
+
+// The randomized eigendecomposition of B_{n+1} - B0 (Algorithm 3): probes
+// X (given, or Philox normals), E = (B - B0) X, a rank-revealing orthonormal
+// basis Q of E's rows; then either the single pass of Algorithm 3 (Omega
+// from Omega (Q^T X) = Q^T E) or, two_pass, the Rayleigh-Ritz second pass
+// C = Q (B - B0) Q^T.  Eigenpairs, V = U^T Q and the posterior std follow.
+int lowrank_randomized(gbfwi_bfgs *h, const float *X, int p, int rank, unsigned long long seed, double eps_prior,
+                       float *V, double *lambda, float *std_out, bool two_pass, cudaStream_t s)
 {
-    if (!h || p < 1 || p > 256 || rank < 1 || rank > p || !(eps_prior > 0)) return GBFWI_EINVAL;
-    GB_TRY(gb_check_local(X, V, lambda, std_out));
-    cudaStream_t s = (cudaStream_t)stream;
     const long long n = h->n, ld = h->ld;
     const int k = h->k;
     // the probe block in a store buffer (aligned rows for the tensor cores)
@@ -1106,12 +1122,27 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
         std::swap(Q, Qf);                 // Q: current basis; Qf: free
     }
     std::swap(Q, Qf);                     // Qf: the basis; Q: free
-    // 3. [Q^T E, Q^T X] in one pass over Q (Omega = (Q^T E)(Q^T X)^-1
-    //    amplifies their error by cond(Q^T X)); Omega by least squares; eigenpairs
-    GB_TRY(atb(h, Qf, nullptr, r, r, E, Xd, p, 2 * p, QEX, 2 * p, s));
-    omega_ls_kernel<<<1, 512, use_smem ? ws : 0, s>>>(QEX, QEX + p, 2 * p, r, p, rank, work, lam, coef, flag,
-                                                      use_smem);
-    GB_LAUNCHED();
+    if (!two_pass) {
+        // 3. [Q^T E, Q^T X] in one pass over Q (Omega = (Q^T E)(Q^T X)^-1
+        //    amplifies their error by cond(Q^T X)); Omega by least squares; eigenpairs
+        GB_TRY(atb(h, Qf, nullptr, r, r, E, Xd, p, 2 * p, QEX, 2 * p, s));
+        omega_ls_kernel<<<1, 512, use_smem ? ws : 0, s>>>(QEX, QEX + p, 2 * p, r, p, rank, work, lam, coef, flag,
+                                                          use_smem);
+        GB_LAUNCHED();
+    } else {
+        // 3. second pass: E2 = (B - B0) Q (into E, free now), C = Q E2^T
+        //    (the Rayleigh-Ritz matrix, symmetrised), its eigenpairs
+        GB_TRY(apply_dev(h, Qf, ld, r, E, ld, 1.0, 1, s));
+        GB_TRY(atb(h, Qf, nullptr, r, r, E, nullptr, r, r, G, r, s));
+        sym_kernel<<<1, 256, 0, s>>>(G, r);
+        GB_LAUNCHED();
+        const size_t we = ((size_t)r * r + r + 16 + ((size_t)r + 2) * (r + 2) / 4) * sizeof(double);
+        const int use_smem2 = we <= 200 * 1024;
+        if (use_smem2)
+            GB_CUDA(cudaFuncSetAttribute(eig_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)we));
+        eig_select_kernel<<<1, 512, use_smem2 ? we : 0, s>>>(G, r, rank, work, lam, coef, flag, use_smem2);
+        GB_LAUNCHED();
+    }
     // 4. V = Q U (first `rank` eigenvectors; rows beyond r are zero)
     const bool devV = V && gb_is_device_ptr(V);
     float *Vd = devV ? V : E;             // E buffer is free now
@@ -1138,6 +1169,24 @@ extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int r
         return gb_nonfinite(stage[flag_h >= 1 && flag_h <= 4 ? flag_h : 0]);
     }
     return GBFWI_OK;
+}
+
+}  // namespace
+
+extern "C" int gbfwi_lowrank_invhess(gbfwi_bfgs *h, const float *X, int p, int rank, unsigned long long seed,
+                                     double eps_prior, float *V, double *lambda, float *std_out, void *stream)
+{
+    if (!h || p < 1 || p > 256 || rank < 1 || rank > p || !(eps_prior > 0)) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(X, V, lambda, std_out));
+    return lowrank_randomized(h, X, p, rank, seed, eps_prior, V, lambda, std_out, false, (cudaStream_t)stream);
+}
+
+extern "C" int gbfwi_lowrank_twopass(gbfwi_bfgs *h, const float *X, int p, int rank, unsigned long long seed,
+                                     double eps_prior, float *V, double *lambda, float *std_out, void *stream)
+{
+    if (!h || p < 1 || p > 256 || rank < 1 || rank > p || !(eps_prior > 0)) return GBFWI_EINVAL;
+    GB_TRY(gb_check_local(X, V, lambda, std_out));
+    return lowrank_randomized(h, X, p, rank, seed, eps_prior, V, lambda, std_out, true, (cudaStream_t)stream);
 }
 
 extern "C" int gbfwi_lowrank_exact(gbfwi_bfgs *h, int rank, double eps_prior, float *V, double *lambda,

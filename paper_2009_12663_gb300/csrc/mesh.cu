@@ -121,7 +121,6 @@ extern "C" const char *gbfwi_strerror(int code)
     case GBFWI_ECFL: return "time step violates the stability bound dt*vp_max/dx_min <= 0.5";
     case GBFWI_ECURV: return "BFGS pair rejected (curvature y^T s <= 0)";
     case GBFWI_ENONFINITE: return g_nonfinite[0] ? g_nonfinite : "non-finite value";
-    case GBFWI_ETIMEOUT: return "device-side wait timed out";
     case GBFWI_ENOMODEL: return "no model set";
     case GBFWI_ESCRATCH: return "request exceeds the fixed scratch of a no-allocation entry point (at most 256 shots)";
     }

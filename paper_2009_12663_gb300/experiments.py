@@ -2,7 +2,8 @@
 synthetic models (Section 3: BFGS vs L-BFGS(5), preconditioners P1-P4,
 RSVD uncertainty maps compared with the true model error).
 
-    python -m paper_2009_12663_gb300.experiments [--iterations 15] [--out result.json]
+    python -m paper_2009_12663_gb300.experiments [--iterations 15] [--workload small|marmousi340x70]
+                                                 [--out result.json]
     python -m paper_2009_12663_gb300.experiments --learned [--train-pairs 48] [--train-steps 2000]
                                                  [--lr-decay 0.999] [--out result.json]
 
@@ -53,26 +54,50 @@ def build(nex=80, nez=20, h=50.0, nshot=8, f0=8.0, nt=3000, seed=11, smooth=250.
     return m, ids, d_obs, true.contiguous(), start.contiguous()
 
 
-def run(iterations=15, sigma=100.0, rank=None):
-    mesh, ids, d_obs, true, start = build()
+WORKLOADS = {
+    "small": dict(nex=80, nez=20, h=50.0, nshot=8, f0=8.0, nt=3000, seed=11, smooth=250.0),
+    # the benchmark's Marmousi-shaped workload: 340 x 70 elements of 50 m,
+    # 24 explosive 5 Hz sources, 341 receivers, dt 0.5 ms, 12000 steps,
+    # starting model the truth blurred by a 500 m Gaussian
+    "marmousi340x70": dict(nex=340, nez=70, h=50.0, nshot=24, f0=5.0, nt=12000, seed=2024, smooth=500.0),
+}
+
+
+def run(iterations=15, sigma=100.0, rank=None, workload="small"):
+    """Section 3 in kind: BFGS, L-BFGS(5) and BFGS with P1-P4, data and
+    model misfit per iteration (Figs. 3 and 5), then for the P4 run the
+    low-rank uncertainty (Section 2.3: single-pass with p = k probes as the
+    paper, the two-pass variant, and the exact decomposition whose rank is
+    at most 2k), the std maps against the true model error, and the
+    Appendix C misfit scan."""
+    w = WORKLOADS[workload]
+    mesh, ids, d_obs, true, start = build(**w)
     prob = Problem(mesh, ids, d_obs, invert=(False, True, True))
     mask = prob.mask
+    one = torch.tensor([True])
     variants = [("BFGS", None, None), ("L-BFGS(5)", None, 5)] + [(f"BFGS+P{k}", k, None) for k in (1, 2, 3, 4)]
-    out = {"model": "marmousi-shaped 80x20 elements of 50 m, 8 shots (8 Hz), 81 receivers, 3000 steps",
-           "inverted": "vp, vs (rho fixed)", "variants": {}}
+    out = {"model": f"marmousi-shaped {w['nex']}x{w['nez']} elements of {w['h']:g} m, {w['nshot']} shots "
+                    f"({w['f0']:g} Hz), {mesh.nrec} receivers, {w['nt']} steps, start = truth blurred by "
+                    f"{w['smooth']:g} m",
+           "inverted": "vp, vs (rho fixed)", "preconditioner_smoothing_sigma_m": sigma, "variants": {}}
     keep = {}
     for name, kind, memory in variants:
         B0 = preconditioner(mesh, ids, start, kind, sigma) if kind else None
         prob.evaluations = {"misfit": 0, "gradient": 0}
+        mm = {"vp": [1.0], "vs": [1.0]}
+
+        def cb(it, mk, h):
+            mm["vp"].append(model_misfit(mk[1:2], true[1:2], start[1:2], one))
+            mm["vs"].append(model_misfit(mk[2:3], true[2:3], start[2:3], one))
+
         t0 = time.perf_counter()
-        m_inv, hist, store = fwi(prob, start, iterations, B0=B0, memory=memory)
+        m_inv, hist, store = fwi(prob, start, iterations, B0=B0, memory=memory, callback=cb)
         wall = time.perf_counter() - t0
         rel = [h["rel_misfit"] for h in hist]
         half = next((h["iteration"] for h in hist if h["rel_misfit"] <= 0.5), None)
         out["variants"][name] = {
             "rel_misfit": rel, "iterations_to_half_misfit": half,
-            "model_misfit_vp": model_misfit(m_inv[1:2], true[1:2], start[1:2], torch.tensor([True])),
-            "model_misfit_vs": model_misfit(m_inv[2:3], true[2:3], start[2:3], torch.tensor([True])),
+            "model_misfit_vp": mm["vp"], "model_misfit_vs": mm["vs"],
             "evaluations": dict(prob.evaluations), "wall_s": wall}
         keep[name] = (m_inv, store)
     # uncertainty of the P4 run (Section 2.3): p = rank = stored pairs (paper), capped at 2k
@@ -89,7 +114,21 @@ def run(iterations=15, sigma=100.0, rank=None):
     stdm = std.reshape(int(mask.sum()), nz, nx).cpu().numpy()
     err = (m_inv - true).abs()[mask.to(true.device)].cpu().numpy()
     corr = [float(np.corrcoef(stdm[c].ravel(), err[c].ravel())[0, 1]) for c in range(stdm.shape[0])]
+    # the spectrum three ways: exact (rank <= 2k), single pass and two pass
+    # with the paper's p = k probes
+    spectra = {}
+    lam2 = torch.zeros(r, dtype=torch.float64, device=true.device)
+    store.lowrank_twopass(p, r, seed=2020, eps_prior=1.0, lam=lam2)
+    spectra["two_pass_p_k"] = lam2.cpu().numpy().tolist()
+    le = torch.zeros(2 * k, dtype=torch.float64, device=true.device)
+    Ve = torch.zeros(2 * k, n, device=true.device)
+    store.lowrank_exact(2 * k, eps_prior=1.0, V=Ve, lam=le)
+    spectra["exact_rank_2k"] = le.cpu().numpy().tolist()
+    Vh = Ve.double()
+    spectra["exact_V_orthonormality_max_error"] = float((Vh @ Vh.T - torch.eye(2 * k, device=Vh.device,
+                                                                              dtype=Vh.dtype)).abs().max())
     out["uq_P4"] = {"pairs": k, "probes": p, "rank": r, "eigenvalues": lam.cpu().numpy().tolist(),
+                    "spectra": spectra,
                     "std_mean_vp": float(stdm[0].mean()), "std_mean_vs": float(stdm[1].mean()),
                     "corr_std_vs_abs_error": {"vp": corr[0], "vs": corr[1]}}
     out["uq_misfit_scan"] = misfit_scan(prob, m_inv, torch.tensor(stdm, device=true.device), mask)
@@ -126,6 +165,8 @@ def misfit_scan(prob, m_inv, std_maps, mask, vmax=250.0, alphas=(-2, -1.5, -1, -
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--iterations", type=int, default=15)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="small",
+                    help="small: 80x20 elements, 8 shots; marmousi340x70: the benchmark's workload")
     ap.add_argument("--learned", action="store_true", help="run the learned-preconditioner comparison")
     ap.add_argument("--train-pairs", type=int, default=48, help="training pairs of the learned comparison")
     ap.add_argument("--train-steps", type=int, default=2000, help="Adam steps of the learned comparison")
@@ -135,7 +176,7 @@ def main():
     if a.learned:
         res = learned_comparison(n_train=a.train_pairs, steps=a.train_steps, lr_decay=a.lr_decay)
     else:
-        res = run(a.iterations)
+        res = run(a.iterations, workload=a.workload)
     txt = json.dumps(res)
     print(txt)
     if a.out:

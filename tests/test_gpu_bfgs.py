@@ -258,3 +258,29 @@ def test_lowrank_ill_conditioned_history():
     big = np.abs(lr) >= 1e-3 * np.abs(lr).max()
     assert np.allclose(lg[big], lr[big], rtol=1e-2), (lg, lr)
     assert np.all(np.abs(lg[~big]) <= 2e-3 * np.abs(lr).max())
+
+
+@pytest.mark.parametrize("n,k,p,rank", [(5000, 12, 16, 10), (30011, 20, 44, 40)])
+def test_two_pass_matches_oracle_two_pass(n, k, p, rank):
+    """The Rayleigh-Ritz (two-pass) variant of Algorithm 3 against the
+    oracle's, on the same probes: eigenvalues 1e-4, eigenvectors by the
+    gap-scaled angle bound; with p >= 2k probes (second case) both are the
+    exact eigendecomposition of B_{n+1} - B0."""
+    b, S, Y, B0 = store(n, k)
+    X = synth.gaussian_block(8, p, n)
+    V = torch.zeros(rank, n, device=DEV)
+    lam = torch.zeros(rank, dtype=torch.float64, device=DEV)
+    std = torch.zeros(n, device=DEV)
+    b.lowrank_twopass(p, rank, eps_prior=1.5, X=t32(X), V=V, lam=lam, std=std)
+    apply = lambda M: ob.probe_block(np.asarray(M, np.float64), S, Y, B0)
+    Vr, lr = ob.rsvd_two_pass(apply, X.astype(np.float64), rank)
+    _, lam_all = ob.rsvd_two_pass(apply, X.astype(np.float64), p)
+    lg = lam.cpu().numpy()
+    assert np.allclose(lg, lr, rtol=1e-4, atol=1e-6 * np.abs(lr).max())
+    _check_vectors(V.cpu().numpy(), Vr, lam_all, rank)
+    assert rel(std.cpu().numpy(), ob.posterior_std(Vr, lr, B0, eps=1.5)) < 1e-4
+    if p >= 2 * k:
+        Ve = torch.zeros(rank, n, device=DEV)
+        le = torch.zeros(rank, dtype=torch.float64, device=DEV)
+        b.lowrank_exact(rank, eps_prior=1.5, V=Ve, lam=le)
+        assert np.allclose(lg, le.cpu().numpy(), rtol=1e-4, atol=1e-6 * np.abs(lr).max())

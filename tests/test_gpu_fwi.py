@@ -67,3 +67,41 @@ def test_p4_preconditioned_run_and_uncertainty_maps(small):
     big = np.abs(lr) >= 1e-3 * np.abs(lr).max()
     assert np.allclose(lg[big], lr[big], rtol=1e-2), (lg, lr)
     assert np.all(np.abs(lg[~big]) <= 2e-3 * np.abs(lr).max())
+
+
+def test_uncertainty_structure_on_a_real_history(small):
+    """Section 3.2 in kind, on the pairs of a P4-preconditioned inversion:
+    the retrieved inverse Hessian's low-rank part B_{n+1} - B0 = W M W^T
+    (W = [S, B0 Y]) has rank at most 2k (not k, as Section 2.3 states);
+    with p > 2k probes the randomized eigendecomposition (single and two
+    pass) returns no resolved eigenvalue beyond 2k, its resolved spectrum
+    matches the exact decomposition, and the eigenvectors are orthonormal."""
+    mesh, ids, d_obs, true, start = small
+    prob = Problem(mesh, ids, d_obs)
+    B0 = preconditioner(mesh, ids, start, 4, sigma=100.0)
+    m, hist, store = fwi(prob, start, 5, B0=B0)
+    k = store.count
+    assert k >= 3
+    dev = start.device
+    m2 = 2 * k
+    Ve = torch.zeros(m2, store.n, device=dev)
+    le = torch.zeros(m2, dtype=torch.float64, device=dev)
+    store.lowrank_exact(m2, eps_prior=1.0, V=Ve, lam=le)
+    le = le.cpu().numpy()
+    top = np.abs(le).max()
+    resolved = np.abs(le) >= 1e-3 * top
+    assert resolved.sum() <= m2
+    Vh = Ve.double().cpu().numpy()[resolved]
+    assert np.abs(Vh @ Vh.T - np.eye(len(Vh))).max() < 1e-4
+    p = m2 + 6
+    for method in ("lowrank_invhess", "lowrank_twopass"):
+        V = torch.zeros(p, store.n, device=dev)
+        lam = torch.zeros(p, dtype=torch.float64, device=dev)
+        getattr(store, method)(p, p, seed=11, eps_prior=1.0, V=V, lam=lam)
+        lg = lam.cpu().numpy()
+        # nothing resolved beyond 2k directions
+        assert np.all(np.abs(lg[m2:]) <= 2e-3 * top), (method, lg)
+        # the resolved eigenvalues are the exact ones
+        assert np.allclose(lg[:m2][resolved], le[resolved], rtol=1e-2), (method, lg[:m2], le)
+        Vg = V.double().cpu().numpy()[:m2][resolved]
+        assert np.abs(Vg @ Vg.T - np.eye(len(Vg))).max() < 1e-3, method

@@ -127,3 +127,37 @@ def test_philox_gaussian_block_moments():
     assert abs(X.mean()) < 0.01 and abs(X.var() - 1) < 0.01
     assert abs(np.mean(X[0] * X[1])) < 0.02
     assert not np.allclose(X, philox.gaussian_block(12346, 4, 50000))
+
+
+def test_two_pass_rsvd_exact_on_low_rank_and_ritz_bounds():
+    """Two-pass variant: with p >= rank(A) probes it recovers the exact
+    eigenpairs; with fewer, its Ritz values lie inside the spectrum's range
+    and the largest one is within the subspace-iteration bound of the true
+    largest eigenvalue (a single pass has no such guarantee)."""
+    n, r = 300, 8
+    Q, _ = np.linalg.qr(RNG.standard_normal((n, r)))
+    lam = np.array([5.0, -3.0, 2.5, 1.0, -0.7, 0.4, 0.2, 0.05])
+    A = (Q * lam) @ Q.T
+    apply = lambda M: (A @ np.asarray(M).T).T
+    order = np.argsort(-np.abs(lam))
+    V, l = bfgs.rsvd_two_pass(apply, RNG.standard_normal((12, n)), r)
+    assert np.allclose(l, lam[order], rtol=1e-9, atol=1e-12)
+    for k in range(r):
+        assert abs(abs(V[k] @ Q[:, order[k]]) - 1) < 1e-9
+    V4, l4 = bfgs.rsvd_two_pass(apply, RNG.standard_normal((4, n)), 4)
+    assert np.all(l4 <= lam.max() + 1e-12) and np.all(l4 >= lam.min() - 1e-12)
+    assert abs(l4[0]) <= 5.0 + 1e-12 and abs(l4[0]) > 0.5 * 5.0
+    # the Ritz vectors are orthonormal
+    assert np.allclose(V4 @ V4.T, np.eye(4), atol=1e-12)
+
+
+def test_two_pass_rsvd_on_bfgs_history_equals_dense_eigh():
+    n, k = 150, 5
+    S, Y, B0 = _pairs(n, k)
+    apply = lambda M: bfgs.probe_block(np.asarray(M), S, Y, B0)
+    X = RNG.standard_normal((2 * k + 3, n))
+    V, l = bfgs.rsvd_two_pass(apply, X, 2 * k)
+    Ve, le = bfgs.exact_lowrank(S, Y, B0, 2 * k)
+    assert np.allclose(l, le, rtol=1e-8, atol=1e-12 * np.abs(le).max())
+    for j in range(2 * k):
+        assert abs(abs(V[j] @ Ve[j]) - 1) < 1e-7
