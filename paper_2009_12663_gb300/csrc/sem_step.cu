@@ -264,18 +264,11 @@ struct StepShape {
     static constexpr int RPP = NT / CW;                       // owned-node rows per pass
     static constexpr int NC = (MODE == MODE_FWD_PC || MODE == MODE_ADJ_PC) ? 3 : 2;
     static constexpr int NWIN = (MODE == MODE_ADJ_G) ? 4 : 3;  // u, lambda-mu, node sums (+ history)
-    // The adjoint-gradient step reads the owned velocity, 1/M and its three
-    // accumulators straight from global memory (coalesced rows) instead of
-    // staging them: with its four windows only, three CTAs fit on an SM
-    // (12 warps instead of 8; its registers are bounded to match).
-    static constexpr bool STAGE_OWNED = MODE != MODE_ADJ_G;
+    static constexpr int NACC = (MODE == MODE_ADJ_G) ? 3 : 0;  // accumulators staged in shared memory
     static constexpr int WIN4 = (NC == 3) ? (WIN + 3) / 4 * 4 : 0;  // 3rd node-sum plane (floats)
-    static constexpr int MINB = ((MODE == MODE_FWD || MODE == MODE_ADJ_G ? 384 : 256) / NT) > 0
-                                    ? (MODE == MODE_FWD || MODE == MODE_ADJ_G ? 384 : 256) / NT
-                                    : 1;
+    static constexpr int MINB = ((MODE == MODE_FWD ? 384 : 256) / NT) > 0 ? (MODE == MODE_FWD ? 384 : 256) / NT : 1;
     static constexpr size_t bytes = (size_t)NWIN * WIN * sizeof(float2) + (size_t)WIN4 * sizeof(float) +
-                                    (STAGE_OWNED ? (size_t)OZ * OXP * sizeof(float2) + (size_t)OZ * OXQ * sizeof(float)
-                                                 : 0);
+                                    (size_t)OZ * OXP * sizeof(float2) + (size_t)(1 + NACC) * OZ * OXQ * sizeof(float);
     static_assert(NT % CW == 0 && CW >= OX, "owned-node mapping");
 };
 
@@ -293,8 +286,9 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
     float2 *sK = slm + WIN;                              // node sums over the window
     float2 *su2 = sK + WIN;                              // forward-history window (MODE_ADJ_G)
     float *sK3 = reinterpret_cast<float *>(sw + S::NWIN * WIN);   // 3rd node sum (NC == 3)
-    float2 *svh = reinterpret_cast<float2 *>(sK3 + S::WIN4);       // owned half-step velocity (staged modes)
+    float2 *svh = reinterpret_cast<float2 *>(sK3 + S::WIN4);       // owned half-step velocity
     float *sminv = reinterpret_cast<float *>(svh + S::OZ * OXP);
+    float *sacc = sminv + S::OZ * OXQ;                   // [NACC][OZ][OXQ]
 
     const int b = blockIdx.z;
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
@@ -312,9 +306,12 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
     prefetch_window<NWZ, NWXP, NT>(slm, a.lm, ix0, iz0, a.nz, pitch);
     if (MODE == MODE_ADJ_G)
         prefetch_window<NWZ, NWXP, NT>(su2, a.h0 + (long long)b * a.hstride, ix0, iz0, a.nz, pitch);
-    if constexpr (S::STAGE_OWNED) {
-        prefetch_owned2<OXP, NT>(svh, a.vh + fo, ixo, izo, ow, oh, pitch);
-        prefetch_owned1<OXQ, NT>(sminv, a.minv, ixo, izo, ow, oh, pitch);
+    prefetch_owned2<OXP, NT>(svh, a.vh + fo, ixo, izo, ow, oh, pitch);
+    prefetch_owned1<OXQ, NT>(sminv, a.minv, ixo, izo, ow, oh, pitch);
+    if (MODE == MODE_ADJ_G) {
+        const float *ab = a.acc + (long long)b * a.acc_shot_stride;
+        for (int c = 0; c < 3; ++c)
+            prefetch_owned1<OXQ, NT>(sacc + c * S::OZ * OXQ, ab + c * a.acc_comp_stride, ixo, izo, ow, oh, pitch);
     }
     for (int q = threadIdx.x; q < WIN; q += NT) sK[q] = make_float2(0.f, 0.f);
     cp_async_wait_all();
@@ -405,7 +402,7 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
         const int wq = (oz + 4) * NWXP + ox + 4;
         const long long g = (long long)iz * pitch + ix;
         float2 k = sK[wq];
-        float2 v = S::STAGE_OWNED ? svh[oz * OXP + ox] : a.vh[fo + g];
+        float2 v = svh[oz * OXP + ox];
         const bool edge = (ix == 0) | (ix == a.nx - 1) | (iz == 0) | (iz == a.nz - 1);
         float ax, az;
         if (edge) {
@@ -413,7 +410,7 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
             ax = -(k.x + bd.x * v.x) * bd.z;
             az = -(k.y + bd.y * v.y) * bd.w;
         } else {
-            float mi = S::STAGE_OWNED ? sminv[oz * OXQ + ox] : a.minv[g];
+            float mi = sminv[oz * OXQ + ox];
             ax = -k.x * mi;
             az = -k.y * mi;
         }
@@ -426,11 +423,11 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
             acc[0] += fmaf(ax, ax, az * az);
         } else if (MODE == MODE_ADJ_G) {
             float2 uk = su2[wq];
-            float *acc = a.acc + (long long)b * a.acc_shot_stride + g;
-            const long long cs = a.acc_comp_stride;
             // u_k . a^w; the node's mass factor rho W_g enters once, in the chain rule
-            acc[2 * cs] += fmaf(uk.x, ax, uk.y * az);
+            sacc[2 * S::OZ * OXQ + oz * OXQ + ox] += fmaf(uk.x, ax, uk.y * az);
             if (edge) {
+                float *acc = a.acc + (long long)b * a.acc_shot_stride + g;
+                const long long cs = a.acc_comp_stride;
                 float4 w4 = a.bw[g];
                 float vx = 0.5f * (v.x + vn.x), vz = 0.5f * (v.y + vn.y);
                 acc[3 * cs] += fmaf(w4.x * uk.x, vx, w4.y * uk.y * vz);
@@ -501,8 +498,10 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
         float *acc = a.acc + (long long)b * a.acc_shot_stride + g;
         const long long cs = a.acc_comp_stride;
         if (MODE == MODE_ADJ_G) {
-            acc[0] += k.x;
-            acc[cs] += k.y;
+            const int so = oz * OXQ + ox;
+            acc[0] = sacc[so] + k.x;
+            acc[cs] = sacc[S::OZ * OXQ + so] + k.y;
+            acc[2 * cs] = sacc[2 * S::OZ * OXQ + so];
         } else {
             acc[cs] += k.x;
             acc[2 * cs] += k.y;

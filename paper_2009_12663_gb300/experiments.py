@@ -3,7 +3,7 @@ synthetic models (Section 3: BFGS vs L-BFGS(5), preconditioners P1-P4,
 RSVD uncertainty maps compared with the true model error).
 
     python -m paper_2009_12663_gb300.experiments [--iterations 15] [--workload small|marmousi340x70]
-                                                 [--out result.json]
+                                                 [--variants BFGS+P4] [--probes 60] [--rank 50] [--out result.json]
     python -m paper_2009_12663_gb300.experiments --learned [--train-pairs 48] [--train-steps 2000]
                                                  [--lr-decay 0.999] [--out result.json]
 
@@ -63,7 +63,7 @@ WORKLOADS = {
 }
 
 
-def run(iterations=15, sigma=100.0, rank=None, workload="small"):
+def run(iterations=15, sigma=100.0, rank=None, workload="small", variants=None, probes=None):
     """Section 3 in kind: BFGS, L-BFGS(5) and BFGS with P1-P4, data and
     model misfit per iteration (Figs. 3 and 5), then for the P4 run the
     low-rank uncertainty (Section 2.3: single-pass with p = k probes as the
@@ -75,7 +75,10 @@ def run(iterations=15, sigma=100.0, rank=None, workload="small"):
     prob = Problem(mesh, ids, d_obs, invert=(False, True, True))
     mask = prob.mask
     one = torch.tensor([True])
-    variants = [("BFGS", None, None), ("L-BFGS(5)", None, 5)] + [(f"BFGS+P{k}", k, None) for k in (1, 2, 3, 4)]
+    allv = [("BFGS", None, None), ("L-BFGS(5)", None, 5)] + [(f"BFGS+P{k}", k, None) for k in (1, 2, 3, 4)]
+    variants = [v for v in allv if variants is None or v[0] in variants]
+    if not any(v[0] == "BFGS+P4" for v in variants):
+        raise ValueError("the uncertainty step needs the BFGS+P4 run")
     out = {"model": f"marmousi-shaped {w['nex']}x{w['nez']} elements of {w['h']:g} m, {w['nshot']} shots "
                     f"({w['f0']:g} Hz), {mesh.nrec} receivers, {w['nt']} steps, start = truth blurred by "
                     f"{w['smooth']:g} m",
@@ -103,7 +106,7 @@ def run(iterations=15, sigma=100.0, rank=None, workload="small"):
     # uncertainty of the P4 run (Section 2.3): p = rank = stored pairs (paper), capped at 2k
     m_inv, store = keep["BFGS+P4"]
     k = store.count
-    p = max(2, min(2 * k, k if rank is None else rank))
+    p = max(2, min(2 * k, k if rank is None else rank)) if probes is None else int(probes)
     r = min(p, k if rank is None else rank)
     n = store.n
     V = torch.zeros(r, n, device=true.device)
@@ -167,6 +170,10 @@ def main():
     ap.add_argument("--iterations", type=int, default=15)
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="small",
                     help="small: 80x20 elements, 8 shots; marmousi340x70: the benchmark's workload")
+    ap.add_argument("--variants", default=None,
+                    help="comma-separated subset of BFGS, L-BFGS(5), BFGS+P1..BFGS+P4 (default: all)")
+    ap.add_argument("--probes", type=int, default=None, help="probes p of the uncertainty step (default k)")
+    ap.add_argument("--rank", type=int, default=None, help="rank of the uncertainty step (default k)")
     ap.add_argument("--learned", action="store_true", help="run the learned-preconditioner comparison")
     ap.add_argument("--train-pairs", type=int, default=48, help="training pairs of the learned comparison")
     ap.add_argument("--train-steps", type=int, default=2000, help="Adam steps of the learned comparison")
@@ -176,7 +183,8 @@ def main():
     if a.learned:
         res = learned_comparison(n_train=a.train_pairs, steps=a.train_steps, lr_decay=a.lr_decay)
     else:
-        res = run(a.iterations, workload=a.workload)
+        res = run(a.iterations, workload=a.workload, rank=a.rank, probes=a.probes,
+                  variants=None if a.variants is None else a.variants.split(","))
     txt = json.dumps(res)
     print(txt)
     if a.out:
