@@ -28,7 +28,7 @@ import statistics
 from . import Mesh, num_tiles
 
 CACHE = os.environ.get("GBFWI_AUTOTUNE_CACHE", os.path.expanduser("~/.cache/gbfwi/autotune.json"))
-VERSION = 2
+VERSION = 3
 
 
 def _signature(nex, nez, nshot, nrec, nt, gpu_name, space):

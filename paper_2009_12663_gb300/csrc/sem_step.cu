@@ -16,8 +16,7 @@
 // column also owns the mesh's last node line).  It recomputes the element
 // column to the left and the element row above the tile (halo elements), so
 // every owned node receives all of its element contributions from this CTA:
-// assembly is a fixed-order gather in shared memory, with no atomics and no
-// colouring passes, and the result is bitwise reproducible.
+// no atomics, a fixed summation order, bitwise reproducible results.
 //
 // One thread computes one element: the 25-point tensor-product derivatives
 // with the GLL derivative matrix held in constant memory (uniform operands),
@@ -26,6 +25,12 @@
 // weight is w_i w_j (h/2)^2, the h factors cancel in the element force
 // f_a(m,n) = sum_i D[i][m] tau_ax(i,n) + sum_j D[j][n] tau_az(m,j),
 // tau = w_i w_j sigma_hat, sigma_hat built from derivatives in xi/eta.
+//
+// Assembly: in the forward and adjoint-gradient steps every element owns 16
+// nodes of its patch and receives its neighbours' shares by warp shuffles
+// (x) and one shared-memory exchange (z), then updates its own nodes
+// (sem_step_kernel); the preconditioner steps sum into a shared node array
+// in four colour passes (sem_pc_step_kernel).
 
 #include "gbfwi_internal.h"
 
@@ -73,46 +78,6 @@ __device__ __forceinline__ void grad_at(const float (&px)[25], const float (&pz)
         d = fmaf(cD[j * 5 + k], pz[k * 5 + i], d);
     }
     xx = a; xz = b; zx = c; zz = d;
-}
-
-// element nodal forces (K u restricted to one element) -> out[25]
-template <int NWXP>
-__device__ __forceinline__ void element_force(const float2 *__restrict__ sw, const float2 *__restrict__ slm,
-                                              int base, float2 (&out)[25])
-{
-    float px[25], pz[25];
-    load_patch<NWXP>(sw, base, px, pz);
-    float txx[25], tzz[25], txz[25];
-#pragma unroll
-    for (int j = 0; j < 5; ++j)
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            float xx, xz, zx, zz;
-            grad_at(px, pz, i, j, xx, xz, zx, zz);
-            float2 lm = slm[base + j * NWXP + i];
-            float l2m = fmaf(2.f, lm.y, lm.x);
-            float ww = cW[j * 5 + i];
-            txx[j * 5 + i] = ww * fmaf(l2m, xx, lm.x * zz);
-            tzz[j * 5 + i] = ww * fmaf(lm.x, xx, l2m * zz);
-            txz[j * 5 + i] = ww * (lm.y * (xz + zx));
-        }
-#pragma unroll
-    for (int n = 0; n < 5; ++n)
-#pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            float fx = 0.f, fz = 0.f;
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                fx = fmaf(cD[i * 5 + m], txx[n * 5 + i], fx);
-                fz = fmaf(cD[i * 5 + m], txz[n * 5 + i], fz);
-            }
-#pragma unroll
-            for (int j = 0; j < 5; ++j) {
-                fx = fmaf(cD[j * 5 + n], txz[j * 5 + m], fx);
-                fz = fmaf(cD[j * 5 + n], tzz[j * 5 + m], fz);
-            }
-            out[n * 5 + m] = make_float2(fx, fz);
-        }
 }
 
 // Per local point products of the unscaled strains of two fields A and B,
@@ -167,6 +132,55 @@ __device__ __forceinline__ void element_squares(const float2 *__restrict__ wa, i
             out[q + 1] = ww * fmaf(axx, axx, azz * azz);
             out[q + 2] = ww * (ga * ga);
         }
+}
+
+// Element nodal forces accumulated row by row of local points: the
+// stresses of row j give the xi-part of the nodes of row j and the eta-part
+// of every node, so one row of stresses is live at a time.
+template <int NWXP>
+__device__ __forceinline__ void element_force_rows(const float2 *__restrict__ sw, const float2 *__restrict__ slm,
+                                                   int base, float2 (&f)[25])
+{
+    float px[25], pz[25];
+    load_patch<NWXP>(sw, base, px, pz);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        float txx[5], tzz[5], txz[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            float xx, xz, zx, zz;
+            grad_at(px, pz, i, j, xx, xz, zx, zz);
+            float2 lm = slm[base + j * NWXP + i];
+            float l2m = fmaf(2.f, lm.y, lm.x);
+            float ww = cW[j * 5 + i];
+            txx[i] = ww * fmaf(l2m, xx, lm.x * zz);
+            tzz[i] = ww * fmaf(lm.x, xx, l2m * zz);
+            txz[i] = ww * (lm.y * (xz + zx));
+        }
+        // f(m, n) += D[j][n] (txz, tzz)(m, j) for every node; for n == j also
+        // the xi-part sum_i D[i][m] (txx, txz)(i, j)
+#pragma unroll
+        for (int n = 0; n < 5; ++n)
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                float fx, fz;
+                if (j == 0) {
+                    fx = cD[n] * txz[m];
+                    fz = cD[n] * tzz[m];
+                } else {
+                    fx = fmaf(cD[j * 5 + n], txz[m], f[n * 5 + m].x);
+                    fz = fmaf(cD[j * 5 + n], tzz[m], f[n * 5 + m].y);
+                }
+                if (n == j) {
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) {
+                        fx = fmaf(cD[i * 5 + m], txx[i], fx);
+                        fz = fmaf(cD[i * 5 + m], txz[i], fz);
+                    }
+                }
+                f[n * 5 + m] = make_float2(fx, fz);
+            }
+    }
 }
 
 // window load: rows iz0.., node pairs from ix0 (even); out-of-mesh -> 0.
@@ -252,8 +266,323 @@ __device__ __forceinline__ void prefetch_owned1(float *dst, const float *src, in
     }
 }
 
+// ---------------------------------------------------------------------------
+// Forward and adjoint-gradient steps (MODE_FWD, MODE_ADJ_G): owner-computes assembly
+// ---------------------------------------------------------------------------
+// Each element owns the 16 nodes (i, j) in [0,4) x [0,4) of its patch (the
+// last element of a mesh row / column also owns its i = 4 column / j = 4
+// row), so the tile's owned nodes are partitioned among the element
+// threads.  Assembly of the element vectors is then two exchanges instead
+// of colour passes over a node-sum array:
+//   x: the i = 4 column of every element goes to its right neighbour, the
+//      next lane of the same warp (a warp holds whole rows of the extended
+//      tile), by register shuffles;
+//   z: the j = 4 row (after the x-step) goes to the element below through a
+//      small shared buffer, after one barrier.
+// Node (0, 0) of element (ex, ez) thus sums
+//   [v(ex,ez) + v(ex-1,ez)(4,.)] + [v(ex,ez-1)(.,4) + v(ex-1,ez-1)(4,4)]
+// in this order for every tile shape, so results are bitwise the same
+// across tile shapes, batching and checkpointing.  The element thread then
+// runs the Newmark update (and the correlation sums) of its own nodes, with
+// 16-byte global accesses along node rows.
+
 template <int TX, int TZ, int MODE>
 struct StepShape {
+    static_assert(MODE == MODE_FWD || MODE == MODE_ADJ_G, "forward and adjoint-gradient modes");
+    static constexpr int NT = (TX + 1) * (TZ + 1);
+    static constexpr int NWZ = 4 * TZ + 5, NWXP = 4 * TX + 6;
+    static constexpr int WIN = NWZ * NWXP;
+    static constexpr int OX = 4 * TX + 1, OZ = 4 * TZ + 1;
+    static constexpr int OXP = 4 * TX + 2;                     // float2 row pitch of the source-force box
+    static constexpr int NWIN = (MODE == MODE_ADJ_G) ? 3 : 2;   // field, (lambda, mu) / source forces, history
+    static constexpr int NZB = (MODE == MODE_ADJ_G) ? 2 : 1;    // z-exchange buffers (force, correlation)
+    static constexpr size_t ZB = (size_t)NT * 5 * sizeof(float2);
+    static_assert((size_t)OZ * OXP <= (size_t)WIN, "source-force box fits the (lambda, mu) window");
+    static constexpr int MINB = ((MODE == MODE_FWD ? 512 : 384) / NT) > 0 ? (MODE == MODE_FWD ? 512 : 384) / NT : 1;
+    static constexpr size_t bytes = (size_t)NWIN * WIN * sizeof(float2) + NZB * ZB;
+};
+
+// x-step of the assembly: v(0, j) += left neighbour's v(4, j) (lane - 1)
+__device__ __forceinline__ void assemble_x(float2 (&v)[25], bool has_left)
+{
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const float rx = __shfl_up_sync(0xffffffffu, v[j * 5 + 4].x, 1);
+        const float rz = __shfl_up_sync(0xffffffffu, v[j * 5 + 4].y, 1);
+        if (has_left) {
+            v[j * 5].x += rx;
+            v[j * 5].y += rz;
+        }
+    }
+}
+
+template <int TX, int TZ, int MODE>
+__global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ, MODE>::MINB)
+    sem_step_kernel(const StepArgs a)
+{
+    using S = StepShape<TX, TZ, MODE>;
+    constexpr int NT = S::NT, NWXP = S::NWXP, NWZ = S::NWZ, WIN = S::WIN, OXP = S::OXP;
+
+    extern __shared__ float4 smem4[];
+    float2 *sw = reinterpret_cast<float2 *>(smem4);     // field window (u_{n+1} or w_{j+1})
+    float2 *slm = sw + WIN;                              // (lambda, mu) window
+    float2 *sF = slm;                                    // source forces of the owned box, after the forces
+    float2 *su2 = slm + WIN;                             // forward-history window (MODE_ADJ_G)
+    float2 *zb0 = sw + S::NWIN * WIN;                    // z-exchange of the forces [NT][5]
+    float2 *zb1 = zb0 + NT * 5;                          // z-exchange of the correlation (MODE_ADJ_G)
+
+    const int b = blockIdx.z;
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    const int ex0 = blockIdx.x * TX, ez0 = blockIdx.y * TZ;
+    const int ix0 = 4 * ex0 - 4, iz0 = 4 * ez0 - 4;
+    const int pitch = a.pitch;
+    const long long fo = (long long)b * a.fstride;
+
+    // ---- phase 0: asynchronous prefetch of the windows
+    prefetch_window<NWZ, NWXP, NT>(sw, a.ucur + fo, ix0, iz0, a.nz, pitch);
+    prefetch_window<NWZ, NWXP, NT>(slm, a.lm, ix0, iz0, a.nz, pitch);
+    if (MODE == MODE_ADJ_G)
+        prefetch_window<NWZ, NWXP, NT>(su2, a.h0 + (long long)b * a.hstride, ix0, iz0, a.nz, pitch);
+    cp_async_wait_all();
+    __syncthreads();
+
+    // ---- phase 1: records, element forces
+    if (MODE == MODE_FWD && a.seis) {
+        int rb = a.rec_tptr[tile], re = a.rec_tptr[tile + 1];
+        for (int t = threadIdx.x; t < 2 * (re - rb); t += NT) {
+            int r = a.rec_list[rb + (t >> 1)], c = t & 1;
+            int2 e = a.rec_e[r];
+            int base = (4 * (e.y - ez0 + 1)) * NWXP + 4 * (e.x - ex0 + 1);
+            const float *w = a.recw + r * 25;
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+#pragma unroll
+                for (int i = 0; i < 5; ++i) {
+                    float2 v = sw[base + j * NWXP + i];
+                    s = fmaf(w[j * 5 + i], c ? v.y : v.x, s);
+                }
+            a.seis[(long long)b * a.seis_shot_stride + (long long)(r * 2 + c) * a.nt + a.trec] = s;
+        }
+    }
+    constexpr int R = 32 / (TX + 1);
+    static_assert(R >= 1 && 32 % (TX + 1) == 0 && (TZ + 1) % (2 * R) == 0, "parity-grouped element rows");
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int elx = lane % (TX + 1);
+    const int elz = (wid >> 1) * 2 * R + (wid & 1) + 2 * (lane / (TX + 1));
+    const int ex = ex0 - 1 + elx, ez = ez0 - 1 + elz;
+    const bool evalid = (ex >= 0) && (ez >= 0) && (ex < a.nex) && (ez < a.nez);
+    const bool owns = evalid && elx >= 1 && elz >= 1;    // halo elements own no node of this tile
+    const int ni = (ex == a.nex - 1) ? 5 : 4, nj = (ez == a.nez - 1) ? 5 : 4;
+    const int ebase = 4 * elz * NWXP + 4 * elx;
+    const int eslot = elz * (TX + 1) + elx;
+    // element below in z (elz - 1) in the same extended-tile column
+    const int bslot = eslot - (TX + 1);
+
+    // owned-node data of the 16 standard nodes (i, j < 4) read from global
+    // memory ahead of their use, 16 bytes at a time along node rows (the
+    // extra column / row of the last element is read where it is used)
+    float2 *vhb = a.vh + fo;
+    float *accb = a.acc + (long long)b * a.acc_shot_stride;
+    const long long cs = a.acc_comp_stride;
+    const long long g00 = (long long)(4 * ez) * pitch + 4 * ex;   // node (0, 0) of the element
+    float2 vhp[16];
+    float mip[16], amp[16];
+    float2 f[25];
+    if (evalid) {
+        element_force_rows<NWXP>(sw, slm, ebase, f);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 25; ++q) f[q] = make_float2(0.f, 0.f);
+    }
+    if (owns) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long long g = g00 + (long long)j * pitch;
+            const float4 v01 = *reinterpret_cast<const float4 *>(vhb + g);
+            const float4 v23 = *reinterpret_cast<const float4 *>(vhb + g + 2);
+            const float4 m4 = *reinterpret_cast<const float4 *>(a.minv + g);
+            vhp[4 * j + 0] = make_float2(v01.x, v01.y);
+            vhp[4 * j + 1] = make_float2(v01.z, v01.w);
+            vhp[4 * j + 2] = make_float2(v23.x, v23.y);
+            vhp[4 * j + 3] = make_float2(v23.z, v23.w);
+            mip[4 * j + 0] = m4.x; mip[4 * j + 1] = m4.y; mip[4 * j + 2] = m4.z; mip[4 * j + 3] = m4.w;
+            if (MODE == MODE_ADJ_G) {
+                const float4 c4 = *reinterpret_cast<const float4 *>(accb + 2 * cs + g);
+                amp[4 * j + 0] = c4.x; amp[4 * j + 1] = c4.y; amp[4 * j + 2] = c4.z; amp[4 * j + 3] = c4.w;
+            }
+        }
+    }
+    assemble_x(f, elx >= 1);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) zb0[eslot * 5 + i] = f[20 + i];
+    __syncthreads();                                     // windows read, z-row published
+
+    // ---- sources (tiles with injections only): forces of the owned box
+    const int src_id = a.shot_map ? a.shot_map[b] : b;
+    const int *gp = a.gptr + (a.per_shot_groups ? (long long)src_id * (a.ntiles + 1) : 0);
+    const int gb = gp[tile], ge = gp[tile + 1];
+    if (ge > gb) {
+        for (int q = threadIdx.x; q < S::OZ * OXP; q += NT) sF[q] = make_float2(0.f, 0.f);
+        __syncthreads();
+        const float *sig = a.sig + (long long)src_id * a.sig_shot_stride + a.tsig;
+        for (int g = gb + threadIdx.x; g < ge; g += NT) {
+            InjGroup G = a.groups[g];
+            float fx = 0.f, fz = 0.f;
+            for (int q = G.begin; q < G.end; ++q) {
+                InjEntry E = a.entries[q];
+                fx = fmaf(E.wx, sig[(long long)E.cx * a.sig_chan_stride], fx);
+                fz = fmaf(E.wz, sig[(long long)E.cz * a.sig_chan_stride], fz);
+            }
+            int oz = G.node / S::OX, ox = G.node - oz * S::OX;
+            sF[oz * OXP + ox] = make_float2(-fx * a.sig_scale, -fz * a.sig_scale);
+        }
+        __syncthreads();
+    }
+
+    // ---- phase 2: z-step of the forces, Newmark update of the owned nodes
+    if (elz >= 1) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const float2 r = zb0[bslot * 5 + i];
+            f[i].x += r.x;
+            f[i].y += r.y;
+        }
+    }
+    const float dt = a.dt;
+    if (owns) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            float2 vrow[5];                              // new half-step velocity and displacement of the row
+            float2 urow[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                if (!(i < ni && j < nj)) continue;
+                const bool std16 = (i < 4) && (j < 4);
+                const int q = j * 5 + i;
+                const int ix = 4 * ex + i, iz = 4 * ez + j;
+                const long long g = g00 + (long long)j * pitch + i;
+                float2 k = f[q];
+                if (ge > gb) {
+                    const float2 F = sF[(4 * (elz - 1) + j) * OXP + 4 * (elx - 1) + i];
+                    k.x += F.x;
+                    k.y += F.y;
+                }
+                const float2 v = std16 ? vhp[4 * j + i] : vhb[g];
+                const bool edge = (ix == 0) | (ix == a.nx - 1) | (iz == 0) | (iz == a.nz - 1);
+                float ax, az;
+                if (edge) {
+                    float4 bd = a.bnd[g];
+                    ax = -(k.x + bd.x * v.x) * bd.z;
+                    az = -(k.y + bd.y * v.y) * bd.w;
+                } else {
+                    const float mi = std16 ? mip[4 * j + i] : a.minv[g];
+                    ax = -k.x * mi;
+                    az = -k.y * mi;
+                }
+                const float2 vn = make_float2(fmaf(dt, ax, v.x), fmaf(dt, az, v.y));
+                const float2 uc = sw[ebase + j * NWXP + i];
+                vrow[i] = vn;
+                urow[i] = make_float2(fmaf(dt, vn.x, uc.x), fmaf(dt, vn.y, uc.y));
+                if (!std16) {
+                    vhb[g] = vrow[i];
+                    a.unext[fo + g] = urow[i];
+                }
+                if (MODE == MODE_ADJ_G) {
+                    const float2 uk = su2[ebase + j * NWXP + i];
+                    // u_k . a^w; the node's mass factor rho W_g enters once, in the chain rule
+                    const float am = std16 ? amp[4 * j + i] : accb[2 * cs + g];
+                    accb[2 * cs + g] = am + fmaf(uk.x, ax, uk.y * az);
+                    if (edge) {
+                        float4 w4 = a.bw[g];
+                        float vx = 0.5f * (v.x + vn.x), vz = 0.5f * (v.y + vn.y);
+                        accb[3 * cs + g] += fmaf(w4.x * uk.x, vx, w4.y * uk.y * vz);
+                        accb[4 * cs + g] += fmaf(w4.z * uk.x, vx, w4.w * uk.y * vz);
+                    }
+                }
+            }
+            if (j < 4) {
+                const long long g = g00 + (long long)j * pitch;
+                *reinterpret_cast<float4 *>(vhb + g) = make_float4(vrow[0].x, vrow[0].y, vrow[1].x, vrow[1].y);
+                *reinterpret_cast<float4 *>(vhb + g + 2) = make_float4(vrow[2].x, vrow[2].y, vrow[3].x, vrow[3].y);
+                float2 *un = a.unext + fo + g;
+                *reinterpret_cast<float4 *>(un) = make_float4(urow[0].x, urow[0].y, urow[1].x, urow[1].y);
+                *reinterpret_cast<float4 *>(un + 2) = make_float4(urow[2].x, urow[2].y, urow[3].x, urow[3].y);
+            }
+        }
+    }
+    if constexpr (MODE == MODE_FWD) return;
+
+    // ---- phase 3: element strain products, assembled like the forces
+    {
+        float pr[50];
+        if (evalid) {
+            element_products<NWXP, 2>(sw, su2, ebase, pr);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 50; ++q) pr[q] = 0.f;
+        }
+        float2 c[25];
+#pragma unroll
+        for (int q = 0; q < 25; ++q) c[q] = make_float2(pr[2 * q], pr[2 * q + 1]);
+        // strain accumulators of the 16 standard nodes, read ahead of the exchange
+        float4 a0p[4], a1p[4];
+        if (owns) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const long long g = g00 + (long long)j * pitch;
+                a0p[j] = *reinterpret_cast<const float4 *>(accb + g);
+                a1p[j] = *reinterpret_cast<const float4 *>(accb + cs + g);
+            }
+        }
+        assemble_x(c, elx >= 1);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) zb1[eslot * 5 + i] = c[20 + i];
+        __syncthreads();
+        if (elz >= 1) {
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                const float2 r = zb1[bslot * 5 + i];
+                c[i].x += r.x;
+                c[i].y += r.y;
+            }
+        }
+        if (owns) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const long long g = g00 + (long long)j * pitch;
+                const float2 *cr = c + j * 5;
+                *reinterpret_cast<float4 *>(accb + g) =
+                    make_float4(a0p[j].x + cr[0].x, a0p[j].y + cr[1].x, a0p[j].z + cr[2].x, a0p[j].w + cr[3].x);
+                *reinterpret_cast<float4 *>(accb + cs + g) =
+                    make_float4(a1p[j].x + cr[0].y, a1p[j].y + cr[1].y, a1p[j].z + cr[2].y, a1p[j].w + cr[3].y);
+            }
+            // the extra column / row of the last element of a mesh row / column
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+#pragma unroll
+                for (int i = 0; i < 5; ++i)
+                    if ((i == 4 || j == 4) && i < ni && j < nj) {
+                        const long long g = g00 + (long long)j * pitch + i;
+                        accb[g] += c[j * 5 + i].x;
+                        accb[cs + g] += c[j * 5 + i].y;
+                    }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Preconditioner steps (MODE_FWD_PC, MODE_ADJ_PC; iteration 0 only)
+// ---------------------------------------------------------------------------
+// The forward step with the P1/P3 time integrals (Eqs. 5 and 7, A21) and
+// the receiver-field step with the P2/P4 integrals (Eqs. 6 and 8, A22).
+// Node sums are gathered in a shared node array over the window, the
+// element contributions added in four passes by global element parity
+// (4-colouring): deterministic and identical for every tile shape.
+
+template <int TX, int TZ, int MODE>
+struct PcShape {
+    static_assert(MODE == MODE_FWD_PC || MODE == MODE_ADJ_PC, "preconditioner modes");
     static constexpr int NT = (TX + 1) * (TZ + 1);          // one thread per element of the extended tile
     static constexpr int NWZ = 4 * TZ + 5, NWXP = 4 * TX + 6;
     static constexpr int WIN = NWZ * NWXP;                    // float2 per window
@@ -262,33 +591,29 @@ struct StepShape {
     static constexpr int OXQ = 4 * TX + 4;                    // float row pitch of owned boxes
     static constexpr int CW = OX <= 32 ? 32 : (OX <= 64 ? 64 : 128);   // owned-node columns per pass
     static constexpr int RPP = NT / CW;                       // owned-node rows per pass
-    static constexpr int NC = (MODE == MODE_FWD_PC || MODE == MODE_ADJ_PC) ? 3 : 2;
-    static constexpr int NWIN = (MODE == MODE_ADJ_G) ? 4 : 3;  // u, lambda-mu, node sums (+ history)
-    static constexpr int NACC = (MODE == MODE_ADJ_G) ? 3 : 0;  // accumulators staged in shared memory
-    static constexpr int WIN4 = (NC == 3) ? (WIN + 3) / 4 * 4 : 0;  // 3rd node-sum plane (floats)
-    static constexpr int MINB = ((MODE == MODE_FWD ? 384 : 256) / NT) > 0 ? (MODE == MODE_FWD ? 384 : 256) / NT : 1;
+    static constexpr int NWIN = 3;                            // field, (lambda, mu) / 2nd field, node sums
+    static constexpr int WIN4 = (WIN + 3) / 4 * 4;            // 3rd node-sum plane (floats)
+    static constexpr int MINB = (256 / NT) > 0 ? 256 / NT : 1;
     static constexpr size_t bytes = (size_t)NWIN * WIN * sizeof(float2) + (size_t)WIN4 * sizeof(float) +
-                                    (size_t)OZ * OXP * sizeof(float2) + (size_t)(1 + NACC) * OZ * OXQ * sizeof(float);
+                                    (size_t)OZ * OXP * sizeof(float2) + (size_t)OZ * OXQ * sizeof(float);
     static_assert(NT % CW == 0 && CW >= OX, "owned-node mapping");
 };
 
 template <int TX, int TZ, int MODE>
-__global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ, MODE>::MINB)
-    sem_step_kernel(const StepArgs a)
+__global__ void __launch_bounds__(PcShape<TX, TZ, MODE>::NT, PcShape<TX, TZ, MODE>::MINB)
+    sem_pc_step_kernel(const StepArgs a)
 {
-    using S = StepShape<TX, TZ, MODE>;
+    using S = PcShape<TX, TZ, MODE>;
     constexpr int NT = S::NT, NWXP = S::NWXP, NWZ = S::NWZ, WIN = S::WIN;
-    constexpr int OXP = S::OXP, OXQ = S::OXQ, CW = S::CW, RPP = S::RPP, NC = S::NC;
+    constexpr int OXP = S::OXP, OXQ = S::OXQ, CW = S::CW, RPP = S::RPP;
 
     extern __shared__ float4 smem4[];
     float2 *sw = reinterpret_cast<float2 *>(smem4);     // field window (u_{n+1} or w_{j+1})
-    float2 *slm = sw + WIN;                              // (lambda, mu) window; 2nd field in P-modes
+    float2 *slm = sw + WIN;                              // (lambda, mu) window; 2nd field later
     float2 *sK = slm + WIN;                              // node sums over the window
-    float2 *su2 = sK + WIN;                              // forward-history window (MODE_ADJ_G)
-    float *sK3 = reinterpret_cast<float *>(sw + S::NWIN * WIN);   // 3rd node sum (NC == 3)
+    float *sK3 = reinterpret_cast<float *>(sw + S::NWIN * WIN);   // 3rd node sum
     float2 *svh = reinterpret_cast<float2 *>(sK3 + S::WIN4);       // owned half-step velocity
     float *sminv = reinterpret_cast<float *>(svh + S::OZ * OXP);
-    float *sacc = sminv + S::OZ * OXQ;                   // [NACC][OZ][OXQ]
 
     const int b = blockIdx.z;
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
@@ -304,45 +629,35 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
     // ---- phase 0: asynchronous prefetch of every input of this step
     prefetch_window<NWZ, NWXP, NT>(sw, a.ucur + fo, ix0, iz0, a.nz, pitch);
     prefetch_window<NWZ, NWXP, NT>(slm, a.lm, ix0, iz0, a.nz, pitch);
-    if (MODE == MODE_ADJ_G)
-        prefetch_window<NWZ, NWXP, NT>(su2, a.h0 + (long long)b * a.hstride, ix0, iz0, a.nz, pitch);
     prefetch_owned2<OXP, NT>(svh, a.vh + fo, ixo, izo, ow, oh, pitch);
     prefetch_owned1<OXQ, NT>(sminv, a.minv, ixo, izo, ow, oh, pitch);
-    if (MODE == MODE_ADJ_G) {
-        const float *ab = a.acc + (long long)b * a.acc_shot_stride;
-        for (int c = 0; c < 3; ++c)
-            prefetch_owned1<OXQ, NT>(sacc + c * S::OZ * OXQ, ab + c * a.acc_comp_stride, ixo, izo, ow, oh, pitch);
-    }
     for (int q = threadIdx.x; q < WIN; q += NT) sK[q] = make_float2(0.f, 0.f);
     cp_async_wait_all();
     __syncthreads();
 
     // ---- phase 1: records, element forces accumulated by colour, sources
-    if (MODE == MODE_FWD || MODE == MODE_FWD_PC) {
-        if (a.seis) {
-            int rb = a.rec_tptr[tile], re = a.rec_tptr[tile + 1];
-            for (int t = threadIdx.x; t < 2 * (re - rb); t += NT) {
-                int r = a.rec_list[rb + (t >> 1)], c = t & 1;
-                int2 e = a.rec_e[r];
-                int base = (4 * (e.y - ez0 + 1)) * NWXP + 4 * (e.x - ex0 + 1);
-                const float *w = a.recw + r * 25;
-                float s = 0.f;
+    if (MODE == MODE_FWD_PC && a.seis) {
+        int rb = a.rec_tptr[tile], re = a.rec_tptr[tile + 1];
+        for (int t = threadIdx.x; t < 2 * (re - rb); t += NT) {
+            int r = a.rec_list[rb + (t >> 1)], c = t & 1;
+            int2 e = a.rec_e[r];
+            int base = (4 * (e.y - ez0 + 1)) * NWXP + 4 * (e.x - ex0 + 1);
+            const float *w = a.recw + r * 25;
+            float s = 0.f;
 #pragma unroll
-                for (int j = 0; j < 5; ++j)
+            for (int j = 0; j < 5; ++j)
 #pragma unroll
-                    for (int i = 0; i < 5; ++i) {
-                        float2 v = sw[base + j * NWXP + i];
-                        s = fmaf(w[j * 5 + i], c ? v.y : v.x, s);
-                    }
-                a.seis[(long long)b * a.seis_shot_stride + (long long)(r * 2 + c) * a.nt + a.trec] = s;
-            }
+                for (int i = 0; i < 5; ++i) {
+                    float2 v = sw[base + j * NWXP + i];
+                    s = fmaf(w[j * 5 + i], c ? v.y : v.x, s);
+                }
+            a.seis[(long long)b * a.seis_shot_stride + (long long)(r * 2 + c) * a.nt + a.trec] = s;
         }
     }
     // Element of this thread.  A warp holds R = 32 / (TX + 1) rows of the
     // extended tile, all of one row parity (rows r, r + 2, ...), so its
     // elements take only two of the four colours below and it runs the
-    // accumulation body in two of the four passes (rows of one half-warp
-    // stay contiguous: the same shared-memory bank pattern as row order).
+    // accumulation body in two of the four passes.
     constexpr int R = 32 / (TX + 1);
     static_assert(R >= 1 && 32 % (TX + 1) == 0 && (TZ + 1) % (2 * R) == 0, "parity-grouped element rows");
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -356,7 +671,7 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
     const int colour = ((ex0 - 1 + elx) & 1) | (((ez0 - 1 + elz) & 1) << 1);
     {
         float2 f[25];
-        if (evalid) element_force<NWXP>(sw, slm, ebase, f);
+        if (evalid) element_force_rows<NWXP>(sw, slm, ebase, f);
 #pragma unroll 1
         for (int pass = 0; pass < 4; ++pass) {
             if (evalid && colour == pass) {
@@ -418,57 +733,41 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
         float2 uc = sw[wq];
         a.vh[fo + g] = vn;
         a.unext[fo + g] = make_float2(fmaf(dt, vn.x, uc.x), fmaf(dt, vn.y, uc.y));
+        float *acc = a.acc + (long long)b * a.acc_shot_stride + g;
         if (MODE == MODE_FWD_PC) {
-            float *acc = a.acc + (long long)b * a.acc_shot_stride + g;
             acc[0] += fmaf(ax, ax, az * az);
-        } else if (MODE == MODE_ADJ_G) {
-            float2 uk = su2[wq];
-            // u_k . a^w; the node's mass factor rho W_g enters once, in the chain rule
-            sacc[2 * S::OZ * OXQ + oz * OXQ + ox] += fmaf(uk.x, ax, uk.y * az);
-            if (edge) {
-                float *acc = a.acc + (long long)b * a.acc_shot_stride + g;
-                const long long cs = a.acc_comp_stride;
-                float4 w4 = a.bw[g];
-                float vx = 0.5f * (v.x + vn.x), vz = 0.5f * (v.y + vn.y);
-                acc[3 * cs] += fmaf(w4.x * uk.x, vx, w4.y * uk.y * vz);
-                acc[4 * cs] += fmaf(w4.z * uk.x, vx, w4.w * uk.y * vz);
-            }
-        } else if (MODE == MODE_ADJ_PC) {
+        } else {
             const long long ho = (long long)b * a.hstride;
             float2 p0 = a.h0[ho + g], p1 = a.h1[ho + g], p2 = a.h2[ho + g];
             float fxa = (p0.x - p1.x) - (p1.x - p2.x);
             float fza = (p0.y - p1.y) - (p1.y - p2.y);
-            float *acc = a.acc + (long long)b * a.acc_shot_stride + g;
             acc[0] += fmaf(fxa, ax, fza * az);
         }
     }
-    if constexpr (MODE == MODE_FWD) return;
     __syncthreads();
 
-    // ---- phase 3: second windows (P-modes) and cleared node sums
+    // ---- phase 3: second windows and cleared node sums
     if (MODE == MODE_FWD_PC) {
         load_window<NWZ, NWXP, NT>(sw, a.uold + fo, nullptr, 1, ix0, iz0, a.nz, pitch);      // u_{n+1} - u_n
-    } else if (MODE == MODE_ADJ_PC) {
+    } else {
         const long long ho = (long long)b * a.hstride;
         load_window<NWZ, NWXP, NT>(slm, a.h0 + ho, a.h1 + ho, 2, ix0, iz0, a.nz, pitch);     // u_{k+1} - u_k
         load_window<NWZ, NWXP, NT>(sw, a.uold + fo, nullptr, 1, ix0, iz0, a.nz, pitch);      // w_{j+1} - w_j
     }
     for (int q = threadIdx.x; q < WIN; q += NT) {
         sK[q] = make_float2(0.f, 0.f);
-        if (NC == 3) sK3[q] = 0.f;
+        sK3[q] = 0.f;
     }
     __syncthreads();
 
     // ---- phase 4: element products accumulated by colour
     {
-        float pr[25 * NC];
+        float pr[75];
         if (evalid) {
             if constexpr (MODE == MODE_FWD_PC)
                 element_squares<NWXP>(sw, ebase, pr);
-            else if constexpr (MODE == MODE_ADJ_G)
-                element_products<NWXP, NC>(sw, su2, ebase, pr);
             else
-                element_products<NWXP, NC>(sw, slm, ebase, pr);
+                element_products<NWXP, 3>(sw, slm, ebase, pr);
         }
 #pragma unroll 1
         for (int pass = 0; pass < 4; ++pass) {
@@ -477,11 +776,11 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
                 for (int j = 0; j < 5; ++j)
 #pragma unroll
                     for (int i = 0; i < 5; ++i) {
-                        int q = ebase + j * NWXP + i, l = (j * 5 + i) * NC;
+                        int q = ebase + j * NWXP + i, l = (j * 5 + i) * 3;
                         float2 &k = sK[q];
                         k.x += pr[l];
                         k.y += pr[l + 1];
-                        if (NC == 3) sK3[q] += pr[l + 2];
+                        sK3[q] += pr[l + 2];
                     }
             }
             __syncthreads();
@@ -497,26 +796,15 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
         float2 k = sK[wq];
         float *acc = a.acc + (long long)b * a.acc_shot_stride + g;
         const long long cs = a.acc_comp_stride;
-        if (MODE == MODE_ADJ_G) {
-            const int so = oz * OXQ + ox;
-            acc[0] = sacc[so] + k.x;
-            acc[cs] = sacc[S::OZ * OXQ + so] + k.y;
-            acc[2 * cs] = sacc[2 * S::OZ * OXQ + so];
-        } else {
-            acc[cs] += k.x;
-            acc[2 * cs] += k.y;
-            acc[3 * cs] += sK3[wq];
-        }
+        acc[cs] += k.x;
+        acc[2 * cs] += k.y;
+        acc[3 * cs] += sK3[wq];
     }
 }
 
 // ---------------------------------------------------------------------------
-
-template <int TX, int TZ, int MODE>
-static size_t step_smem()
-{
-    return StepShape<TX, TZ, MODE>::bytes;
-}
+// launch
+// ---------------------------------------------------------------------------
 
 template <int TX, int TZ, int MODE>
 static int prepare_one()
@@ -525,8 +813,12 @@ static int prepare_one()
     int dev = 0;
     GB_CUDA(cudaGetDevice(&dev));
     if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-        GB_CUDA(cudaFuncSetAttribute(sem_step_kernel<TX, TZ, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)step_smem<TX, TZ, MODE>()));
+        if constexpr (MODE == MODE_FWD || MODE == MODE_ADJ_G)
+            GB_CUDA(cudaFuncSetAttribute(sem_step_kernel<TX, TZ, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)StepShape<TX, TZ, MODE>::bytes));
+        else
+            GB_CUDA(cudaFuncSetAttribute(sem_pc_step_kernel<TX, TZ, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PcShape<TX, TZ, MODE>::bytes));
         attr_done[dev] = true;
     }
     return GBFWI_OK;
@@ -536,10 +828,12 @@ template <int TX, int TZ, int MODE>
 static int launch_one(const StepArgs &a, int nbatch, cudaStream_t s)
 {
     constexpr int NE = (TX + 1) * (TZ + 1);
-    size_t smem = step_smem<TX, TZ, MODE>();
     GB_TRY((prepare_one<TX, TZ, MODE>()));
     dim3 grid((a.nex + TX - 1) / TX, (a.nez + TZ - 1) / TZ, nbatch);
-    sem_step_kernel<TX, TZ, MODE><<<grid, NE, smem, s>>>(a);
+    if constexpr (MODE == MODE_FWD || MODE == MODE_ADJ_G)
+        sem_step_kernel<TX, TZ, MODE><<<grid, NE, StepShape<TX, TZ, MODE>::bytes, s>>>(a);
+    else
+        sem_pc_step_kernel<TX, TZ, MODE><<<grid, NE, PcShape<TX, TZ, MODE>::bytes, s>>>(a);
     GB_LAUNCHED();
     return GBFWI_OK;
 }
@@ -584,10 +878,10 @@ const TileShape kTiles[kNumTiles] = {{15, 7}, {7, 15}, {7, 7}, {15, 15}, {31, 3}
 
 int gb_launch_step(int mode, int tile, const StepArgs &a, int nbatch, cudaStream_t s)
 {
-    // 16-byte copies need 16-byte aligned rows and field bases
+    // 16-byte copies and accesses need 16-byte aligned rows and field bases
     if (a.pitch % 4 != 0 || a.fstride % 2 != 0 || a.hstride % 2 != 0 || a.acc_comp_stride % 4 != 0 ||
-        a.acc_shot_stride % 4 != 0 || ((uintptr_t)a.ucur & 15) || ((uintptr_t)a.vh & 15) ||
-        ((uintptr_t)a.minv & 15) || ((uintptr_t)a.acc & 15) || ((uintptr_t)a.h0 & 15))
+        a.acc_shot_stride % 4 != 0 || ((uintptr_t)a.ucur & 15) || ((uintptr_t)a.unext & 15) ||
+        ((uintptr_t)a.vh & 15) || ((uintptr_t)a.minv & 15) || ((uintptr_t)a.acc & 15) || ((uintptr_t)a.h0 & 15))
         return GBFWI_EINVAL;
     switch (tile) {
     case 0: return launch_mode<15, 7>(mode, a, nbatch, s);
