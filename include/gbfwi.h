@@ -53,7 +53,9 @@ enum {
     GBFWI_ECFL = -4,        /* dt * vp_max / (min GLL node spacing) > 0.5 */
     GBFWI_ECURV = -5,       /* BFGS pair rejected: y^T s <= 1e-12 |s| |y| */
     GBFWI_ENONFINITE = -6,  /* a NaN or Inf reached the seismograms or the model */
-    /* -7 is not used */
+    GBFWI_ETIMEOUT = -7,    /* a time-step kernel's bounded wait for its staged inputs gave up: the
+                               simulation results are invalid.  Reported by the next call on the
+                               mesh that waits for the device (forward into device memory does not) */
     GBFWI_ENOMODEL = -8,    /* simulation requested before gbfwi_set_model */
     GBFWI_ESCRATCH = -9     /* request larger than the fixed scratch of a no-allocation entry point */
 };

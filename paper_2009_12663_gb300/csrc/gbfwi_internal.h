@@ -142,6 +142,7 @@ struct gbfwi_mesh {
     DevBuf w_hist, w_vh, w_adj, w_wh, w_acc, w_snap, w_seis, w_sig, w_obs, w_grad,
         w_red, w_flag, w_shots, w_tmp, w_stage;
     DevBuf w_pc;        // preconditioner accumulators
+    DevBuf w_status;    // int: nonzero after a step kernel's bounded wait gave up
 
     DevBuf w_batch;     // shot ids of the batch being replayed (fixed address for graphs)
     DevBuf w_lacc;      // gradient accumulators of the batch in flight (fixed address for graphs)
@@ -173,6 +174,9 @@ struct gbfwi_mesh {
 };
 
 int gb_build_tile_lists(gbfwi_mesh *m, int tile);
+// after the work on the mesh has completed: GBFWI_ETIMEOUT (and the flag
+// cleared) when a step kernel's bounded wait gave up since the last check
+int gb_take_status(gbfwi_mesh *m);
 
 // ---------------------------------------------------------------------------
 // kernel argument block of the time step (one launch = one step of every
@@ -208,6 +212,8 @@ struct StepArgs {
     float *seis; long long seis_shot_stride; int nt; int trec;
     // accumulators
     float *acc; long long acc_shot_stride; long long acc_comp_stride;
+    // set to 1 when a bounded device-side wait gave up (the step's results are invalid)
+    int *status;
 };
 
 int gb_launch_step(int mode, int tile, const StepArgs &a, int nbatch, cudaStream_t s);

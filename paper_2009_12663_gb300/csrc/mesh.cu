@@ -122,6 +122,7 @@ extern "C" const char *gbfwi_strerror(int code)
     case GBFWI_ECURV: return "BFGS pair rejected (curvature y^T s <= 0)";
     case GBFWI_ENONFINITE: return g_nonfinite[0] ? g_nonfinite : "non-finite value";
     case GBFWI_ENOMODEL: return "no model set";
+    case GBFWI_ETIMEOUT: return "a time-step kernel's bounded wait for its staged inputs gave up";
     case GBFWI_ESCRATCH: return "request exceeds the fixed scratch of a no-allocation entry point (at most 256 shots)";
     }
     return "unknown error";
@@ -303,6 +304,8 @@ extern "C" int gbfwi_mesh_create(const gbfwi_mesh_desc *desc, const gbfwi_source
     if (!rc) rc = m->d_wx.ensure(m->nx * sizeof(float));
     if (!rc) rc = m->d_wz.ensure(m->nz * sizeof(float));
     if (!rc) rc = m->d_recw.ensure(std::max<size_t>(1, m->rec_w.size()) * sizeof(float));
+    if (!rc) rc = m->w_status.ensure(16);
+    if (!rc && cudaMemset(m->w_status.p, 0, 16) != cudaSuccess) rc = GBFWI_ECUDA;
     if (!rc) rc = m->d_rec_e.ensure(std::max(1, nrec) * sizeof(int2));
     if (!rc) rc = m->d_stf.ensure(std::max<size_t>(1, stf.size()) * sizeof(float));
     if (rc) { delete m; return rc; }

@@ -57,6 +57,7 @@ void base_args(StepArgs &a, const Ctx &c)
     a.rec_e = m->d_rec_e.as<int2>();
     a.nt = m->d.nt;
     a.seis_shot_stride = (long long)m->nrec * 2 * m->d.nt;
+    a.status = m->w_status.as<int>();
 }
 
 using SlotFn = std::function<float2 *(int)>;
@@ -130,6 +131,21 @@ int adj_range(const Ctx &c, int mode, int j0, int j1, float2 *wring, float2 *wh,
     }
     return GBFWI_OK;
 }
+
+}  // namespace
+
+int gb_take_status(gbfwi_mesh *m)
+{
+    int st = 0;
+    GB_CUDA(cudaMemcpy(&st, m->w_status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) {
+        GB_CUDA(cudaMemset(m->w_status.p, 0, sizeof(int)));
+        return GBFWI_ETIMEOUT;
+    }
+    return GBFWI_OK;
+}
+
+namespace {
 
 // ------------------------------------------------------------------ kernels
 
@@ -412,7 +428,10 @@ extern "C" int gbfwi_forward(gbfwi_mesh *m, const int *shot_ids, int nshot, floa
             GB_CUDA(cudaMemcpyAsync(seis + seis_shot * i0, out, seis_shot * B * sizeof(float),
                                     cudaMemcpyDeviceToHost, s));
     }
-    if (!dev_out) GB_CUDA(cudaStreamSynchronize(s));
+    if (!dev_out) {
+        GB_CUDA(cudaStreamSynchronize(s));
+        GB_TRY(gb_take_status(m));
+    }
     return GBFWI_OK;
 }
 
@@ -470,6 +489,7 @@ extern "C" int gbfwi_misfit(gbfwi_mesh *m, const int *shot_ids, int nshot, const
     GB_CUDA(cudaMemcpyAsync(&mis_h, mis_d, sizeof(double), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaMemcpyAsync(&flag_h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
+    GB_TRY(gb_take_status(m));
     if (flag_h || !std::isfinite(mis_h)) return gb_nonfinite("misfit");
     *misfit = mis_h;
     return GBFWI_OK;
@@ -810,6 +830,7 @@ extern "C" int gbfwi_adjoint_gradient(gbfwi_mesh *m, const int *shot_ids, int ns
     GB_CUDA(cudaMemcpyAsync(&mis_h, mis_d, sizeof(double), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaMemcpyAsync(&flag_h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
+    GB_TRY(gb_take_status(m));
     if (m->timing) {
         double fm = 0, am = 0;
         for (int bi = 0; bi < nbatch; ++bi) {
@@ -973,6 +994,7 @@ extern "C" int gbfwi_precond_diag(gbfwi_mesh *m, const int *shot_ids, int nshot,
             GB_CUDA(cudaMemcpyAsync(H, Hd, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s));
     }
     GB_CUDA(cudaStreamSynchronize(s));
+    GB_TRY(gb_take_status(m));
     return GBFWI_OK;
 }
 

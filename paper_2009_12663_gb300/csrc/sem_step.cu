@@ -298,9 +298,65 @@ struct StepShape {
     static constexpr int NZB = (MODE == MODE_ADJ_G) ? 2 : 1;    // z-exchange buffers (force, correlation)
     static constexpr size_t ZB = (size_t)NT * 5 * sizeof(float2);
     static_assert((size_t)OZ * OXP <= (size_t)WIN, "source-force box fits the (lambda, mu) window");
+    // half-step velocity of the standard owned nodes (4 TX x 4 TZ), staged in phase 0
+    static constexpr int VXP = 4 * TX;
+    static constexpr size_t VB = (size_t)4 * TZ * VXP * sizeof(float2);
+    static constexpr int NCOPY = NWIN * NWZ + 4 * TZ;           // bulk row copies of phase 0
     static constexpr int MINB = ((MODE == MODE_FWD ? 512 : 384) / NT) > 0 ? (MODE == MODE_FWD ? 512 : 384) / NT : 1;
-    static constexpr size_t bytes = (size_t)NWIN * WIN * sizeof(float2) + NZB * ZB;
+    static constexpr size_t bytes = (size_t)NWIN * WIN * sizeof(float2) + NZB * ZB + VB;
 };
+
+// ---------------------------------------------------------------------------
+// bulk asynchronous copies (TMA unit) completing on a shared-memory mbarrier
+// ---------------------------------------------------------------------------
+
+// bound of a device-side wait: about one second at the SM clock
+constexpr long long kWaitCycles = 2000000000LL;
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *mbar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// the calling thread's arrival, announcing `bytes` of copies
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *mbar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *mbar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// wait for phase `parity` of the barrier; false when the bound ran out
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *mbar, unsigned parity)
+{
+    if (mbar_try_wait(mbar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(mbar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
 
 // x-step of the assembly: v(0, j) += left neighbour's v(4, j) (lane - 1)
 __device__ __forceinline__ void assemble_x(float2 (&v)[25], bool has_left)
@@ -330,6 +386,8 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
     float2 *su2 = slm + WIN;                             // forward-history window (MODE_ADJ_G)
     float2 *zb0 = sw + S::NWIN * WIN;                    // z-exchange of the forces [NT][5]
     float2 *zb1 = zb0 + NT * 5;                          // z-exchange of the correlation (MODE_ADJ_G)
+    float2 *svh = zb0 + S::NZB * NT * 5;                 // [4 TZ][4 TX] owned half-step velocity
+    __shared__ unsigned long long s_mbar;
 
     const int b = blockIdx.z;
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
@@ -338,13 +396,48 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
     const int pitch = a.pitch;
     const long long fo = (long long)b * a.fstride;
 
-    // ---- phase 0: asynchronous prefetch of the windows
-    prefetch_window<NWZ, NWXP, NT>(sw, a.ucur + fo, ix0, iz0, a.nz, pitch);
-    prefetch_window<NWZ, NWXP, NT>(slm, a.lm, ix0, iz0, a.nz, pitch);
-    if (MODE == MODE_ADJ_G)
-        prefetch_window<NWZ, NWXP, NT>(su2, a.h0 + (long long)b * a.hstride, ix0, iz0, a.nz, pitch);
-    cp_async_wait_all();
-    __syncthreads();
+    const int ixo = 4 * ex0, izo = 4 * ez0;              // owned box origin
+    // source injections of this tile (read ahead of their use)
+    const int src_id = a.shot_map ? a.shot_map[b] : b;
+    const int *gp = a.gptr + (a.per_shot_groups ? (long long)src_id * (a.ntiles + 1) : 0);
+    const int gb = gp[tile], ge = gp[tile + 1];
+
+    // ---- phase 0: bulk copies of the windows (rows inside the mesh; the rest
+    // is never read) and of the owned velocity box, one row per copy
+    {
+        const int r_lo = max(0, -iz0), r_hi = min(NWZ, a.nz - iz0);
+        const int cx0 = max(ix0, 0), cx1 = min(ix0 + NWXP, pitch);
+        const unsigned wbytes = (unsigned)(cx1 - cx0) * (unsigned)sizeof(float2);
+        const int vrows = min(4 * TZ, a.nz - izo);
+        const unsigned vbytes = (unsigned)(min(ixo + S::VXP, pitch) - ixo) * (unsigned)sizeof(float2);
+        if (threadIdx.x == 0) {
+            mbar_init(&s_mbar, 1);
+            mbar_arrive_expect_tx(&s_mbar, (unsigned)S::NWIN * (unsigned)(r_hi - r_lo) * wbytes +
+                                               (unsigned)vrows * vbytes);
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < S::NCOPY; c += NT) {
+            if (c < S::NWIN * NWZ) {
+                const int w = c / NWZ, r = c - w * NWZ;
+                const float2 *src = w == 0 ? a.ucur + fo : (w == 1 ? a.lm : a.h0 + (long long)b * a.hstride);
+                float2 *dst = w == 0 ? sw : (w == 1 ? slm : su2);
+                if (r >= r_lo && r < r_hi)
+                    bulk_g2s(dst + r * NWXP + (cx0 - ix0), src + (long long)(iz0 + r) * pitch + cx0, wbytes, &s_mbar);
+            } else {
+                const int r = c - S::NWIN * NWZ;
+                if (r < vrows)
+                    bulk_g2s(svh + r * S::VXP, a.vh + fo + (long long)(izo + r) * pitch + ixo, vbytes, &s_mbar);
+            }
+        }
+        const bool ok = mbar_wait_bounded(&s_mbar, 0);
+        if (__syncthreads_or(!ok)) {
+            // the copies did not complete within the bound: flag it, give the
+            // ones in flight another bounded wait, and leave
+            if (threadIdx.x == 0 && a.status) atomicExch(a.status, 1);
+            mbar_wait_bounded(&s_mbar, 0);
+            return;
+        }
+    }
 
     // ---- phase 1: records, element forces
     if (MODE == MODE_FWD && a.seis) {
@@ -386,7 +479,6 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
     float *accb = a.acc + (long long)b * a.acc_shot_stride;
     const long long cs = a.acc_comp_stride;
     const long long g00 = (long long)(4 * ez) * pitch + 4 * ex;   // node (0, 0) of the element
-    float2 vhp[16];
     float mip[16], amp[16];
     float2 f[25];
     if (evalid) {
@@ -399,13 +491,7 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const long long g = g00 + (long long)j * pitch;
-            const float4 v01 = *reinterpret_cast<const float4 *>(vhb + g);
-            const float4 v23 = *reinterpret_cast<const float4 *>(vhb + g + 2);
             const float4 m4 = *reinterpret_cast<const float4 *>(a.minv + g);
-            vhp[4 * j + 0] = make_float2(v01.x, v01.y);
-            vhp[4 * j + 1] = make_float2(v01.z, v01.w);
-            vhp[4 * j + 2] = make_float2(v23.x, v23.y);
-            vhp[4 * j + 3] = make_float2(v23.z, v23.w);
             mip[4 * j + 0] = m4.x; mip[4 * j + 1] = m4.y; mip[4 * j + 2] = m4.z; mip[4 * j + 3] = m4.w;
             if (MODE == MODE_ADJ_G) {
                 const float4 c4 = *reinterpret_cast<const float4 *>(accb + 2 * cs + g);
@@ -419,9 +505,6 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
     __syncthreads();                                     // windows read, z-row published
 
     // ---- sources (tiles with injections only): forces of the owned box
-    const int src_id = a.shot_map ? a.shot_map[b] : b;
-    const int *gp = a.gptr + (a.per_shot_groups ? (long long)src_id * (a.ntiles + 1) : 0);
-    const int gb = gp[tile], ge = gp[tile + 1];
     if (ge > gb) {
         for (int q = threadIdx.x; q < S::OZ * OXP; q += NT) sF[q] = make_float2(0.f, 0.f);
         __syncthreads();
@@ -468,7 +551,7 @@ __global__ void __launch_bounds__(StepShape<TX, TZ, MODE>::NT, StepShape<TX, TZ,
                     k.x += F.x;
                     k.y += F.y;
                 }
-                const float2 v = std16 ? vhp[4 * j + i] : vhb[g];
+                const float2 v = std16 ? svh[(4 * (elz - 1) + j) * S::VXP + 4 * (elx - 1) + i] : vhb[g];
                 const bool edge = (ix == 0) | (ix == a.nx - 1) | (iz == 0) | (iz == a.nz - 1);
                 float ax, az;
                 if (edge) {
