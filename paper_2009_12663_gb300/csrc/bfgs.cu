@@ -46,6 +46,7 @@ struct gbfwi_bfgs {
     DevBuf X, E, Q, V;         // [p][n] blocks
     DevBuf stage;              // host staging
     DevBuf flag;
+    DevBuf status;             // int: nonzero after a product kernel's bounded wait gave up
     DevBuf ex;                 // FP64 scratch of the exact low-rank decomposition
 };
 
@@ -196,35 +197,53 @@ __global__ void mul_kernel(const float *__restrict__ a, const float *__restrict_
         out[i] = a[i] * b[i];
 }
 
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Compact-form middle product for each column c of T ([2k][p]: rows 0..k-1
 // S^T x_c, rows k..2k-1 (B0 Y)^T x_c):
 //   cv = R^-1 a, top = R^-T ((D + gamma Y^T B0 Y) cv - gamma t2)
 //   coef[c] = [top, -gamma cv]
-__global__ void middle_kernel(const double *__restrict__ T, const double *__restrict__ SY,
-                              const double *__restrict__ YBY, int k, int kmax, int p, double gamma,
-                              double *__restrict__ scratch, float *__restrict__ coef)
+// one warp per probe column c (block c): the k-long FP64 triangular solves
+// and the Y^T B0 Y product, dot products split over the lanes; FP64 is
+// spread over p SMs instead of one
+__global__ void __launch_bounds__(32) middle_kernel(const double *__restrict__ T, const double *__restrict__ SY,
+                                                    const double *__restrict__ YBY, int k, int kmax, int p,
+                                                    double gamma, double *__restrict__ scratch,
+                                                    float *__restrict__ coef)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.x, lane = threadIdx.x;
     if (c >= p) return;
     double *cv = scratch + (long long)c * 2 * k, *d = cv + k;
+    // R cv = T_top (back substitution), R_ij = s_i^T y_j upper
     for (int i = k - 1; i >= 0; --i) {
-        double s = T[(long long)i * p + c];
-        for (int j = i + 1; j < k; ++j) s -= SY[(long long)i * kmax + j] * cv[j];
-        cv[i] = s / SY[(long long)i * kmax + i];
+        double s = 0.0;
+        for (int j = i + 1 + lane; j < k; j += 32) s += __ldg(SY + (long long)i * kmax + j) * cv[j];
+        s = warp_sum(s);
+        if (lane == 0) cv[i] = (__ldg(T + (long long)i * p + c) - s) / __ldg(SY + (long long)i * kmax + i);
+        __syncwarp();
     }
     for (int i = 0; i < k; ++i) {
-        double s = SY[(long long)i * kmax + i] * cv[i];
         double t = 0.0;
-        for (int j = 0; j < k; ++j) t += YBY[(long long)i * kmax + j] * cv[j];
-        d[i] = s + gamma * t - gamma * T[(long long)(k + i) * p + c];
+        for (int j = lane; j < k; j += 32) t += __ldg(YBY + (long long)i * kmax + j) * cv[j];
+        t = warp_sum(t);
+        if (lane == 0)
+            d[i] = __ldg(SY + (long long)i * kmax + i) * cv[i] + gamma * t - gamma * __ldg(T + (long long)(k + i) * p + c);
     }
+    __syncwarp();
     // R^T top = d (forward substitution); overwrite d with top
     for (int i = 0; i < k; ++i) {
-        double s = d[i];
-        for (int j = 0; j < i; ++j) s -= SY[(long long)j * kmax + i] * d[j];
-        d[i] = s / SY[(long long)i * kmax + i];
+        double s = 0.0;
+        for (int j = lane; j < i; j += 32) s += __ldg(SY + (long long)j * kmax + i) * d[j];
+        s = warp_sum(s);
+        if (lane == 0) d[i] = (d[i] - s) / __ldg(SY + (long long)i * kmax + i);
+        __syncwarp();
     }
-    for (int i = 0; i < k; ++i) {
+    for (int i = lane; i < k; i += 32) {
         coef[(long long)c * 2 * k + i] = (float)d[i];
         coef[(long long)c * 2 * k + k + i] = (float)(-gamma * cv[i]);
     }
@@ -237,70 +256,79 @@ __global__ void middle_kernel(const double *__restrict__ T, const double *__rest
 // invertible triangular R that makes the rows nearly orthonormal, since
 // R^-T E spans the rows of E for any invertible R, and the next pass
 // removes what is left; the shift (1e-5 of the trace) keeps the FP32 Gram
-// matrix definite.  The factor and its inverse live in shared memory when
-// 2 p^2 floats fit (use_smem), else in the global scratch A, Rinv.
-__global__ void chol_kernel(const double *__restrict__ G, int p, double shift, float *A, float *Rinv,
-                            float *__restrict__ coef, int *__restrict__ flag, int use_smem)
+// matrix definite.  The Gram matrix, the factor and its inverse live in
+// shared memory when 3 p^2 floats fit (use_smem), else in the global scratch
+// A, Rinv and the coefficient array.
+__global__ void __launch_bounds__(512) chol_kernel(const double *__restrict__ G, int p, double shift, float *A,
+                                                   float *Rinv, float *__restrict__ coef, int *__restrict__ flag,
+                                                   int use_smem)
 {
+    // A: the Gram matrix, then the right-hand sides B of R X = I; R: the
+    // factor (in coef when shared memory is too small); X = R^-1 (in Rinv)
     extern __shared__ float chol_smem[];
+    float *R = coef;
     if (use_smem) {
         A = chol_smem;
-        Rinv = chol_smem + (size_t)p * p;
+        R = chol_smem + (size_t)p * p;
+        Rinv = chol_smem + (size_t)2 * p * p;
     }
-    const int t = threadIdx.x, nt = blockDim.x;
+    // thread (tx, ty) of a 32 x 16 grid owns the elements (ty + 16 i, tx + 32 j):
+    // no index division in the p steps below
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     __shared__ double trace;
-    __shared__ float piv;
-    if (t == 0) {
+    if (threadIdx.x < 32) {
         double tr = 0.0;
-        for (int i = 0; i < p; ++i) tr += G[(long long)i * p + i];
-        trace = tr;
+        for (int i = tx; i < p; i += 32) tr += G[(long long)i * p + i];
+        tr = warp_sum(tr);
+        if (tx == 0) trace = tr;
     }
     __syncthreads();
-    for (int q = t; q < p * p; q += nt) {
-        const int i = q / p, j = q - i * p;
-        A[q] = (float)(G[q] + (i == j ? shift * trace : 0.0));
-    }
+    for (int r = ty; r < p; r += 16)
+        for (int c = tx; c < p; c += 32) A[r * p + c] = (float)(G[(long long)r * p + c] + (r == c ? shift * trace : 0.0));
     __syncthreads();
-    // right-looking factorisation in place: row j of the upper triangle
-    // becomes row j of R
+    // right-looking factorisation, one barrier per step: row j of R is
+    // written from the unscaled row j, which the trailing update reads
     for (int j = 0; j < p; ++j) {
-        if (t == 0) {
-            float dj = A[(long long)j * p + j];
-            if (!(dj > 0.f) || !isfinite(dj)) { *flag = 2; dj = 1.f; }
-            piv = sqrtf(dj);
-            A[(long long)j * p + j] = piv;
+        float dj = A[j * p + j];
+        if (!(dj > 0.f) || !isfinite(dj)) {
+            if (threadIdx.x == 0) *flag = 2;
+            dj = 1.f;
         }
-        __syncthreads();
-        const float inv = 1.f / piv;
-        for (int i = j + 1 + t; i < p; i += nt) A[(long long)j * p + i] *= inv;
-        __syncthreads();
-        const int m = p - j - 1;
-        for (int q = t; q < m * m; q += nt) {
-            const int r = j + 1 + q / m, c = j + 1 + q % m;
-            if (c >= r) A[(long long)r * p + c] = fmaf(-A[(long long)j * p + r], A[(long long)j * p + c], A[(long long)r * p + c]);
+        const float rs = rsqrtf(dj), invd = 1.f / dj;
+        for (int r = ty; r < p; r += 16) {
+            if (r < j) continue;
+            for (int c = tx; c < p; c += 32) {
+                if (c < r) continue;
+                if (r == j) {
+                    R[j * p + c] = c == j ? dj * rs : A[j * p + c] * rs;
+                } else {
+                    A[r * p + c] = fmaf(-A[j * p + r] * invd, A[j * p + c], A[r * p + c]);
+                }
+            }
         }
         __syncthreads();
     }
-    // R^-1 (upper) by back substitution, one column per thread; the
-    // reciprocals of the diagonal go to the (unused) strict lower triangle's
-    // first column (row 0's goes to a shared word)
-    __shared__ float d0inv;
-    for (int i = t; i < p; i += nt)
-        if (i > 0) A[(long long)i * p] = 1.f / A[(long long)i * p + i];
-    if (t == 0) d0inv = 1.f / A[0];
+    // X = R^-1 by the column-oriented back substitution, one barrier per
+    // step: at step i row i of X is final (B[i][c] / R[i][i]) and removed
+    // from the rows above
+    for (int r = ty; r < p; r += 16)
+        for (int c = tx; c < p; c += 32) A[r * p + c] = r == c ? 1.f : 0.f;
     __syncthreads();
-    for (int c = t; c < p; c += nt) {
-        for (int i = c; i >= 0; --i) {
-            float s = (i == c) ? 1.f : 0.f;
-            for (int j = i + 1; j <= c; ++j) s = fmaf(-A[(long long)i * p + j], Rinv[(long long)j * p + c], s);
-            Rinv[(long long)i * p + c] = s * (i == 0 ? d0inv : A[(long long)i * p]);
-        }
+    for (int i = p - 1; i >= 0; --i) {
+        const float rii = 1.f / R[i * p + i];
+        for (int r = ty; r <= i; r += 16)
+            for (int c = tx; c < p; c += 32) {
+                if (c < i) continue;
+                const float xi = A[i * p + c] * rii;
+                if (r == i)
+                    Rinv[i * p + c] = xi;
+                else
+                    A[r * p + c] = fmaf(-R[r * p + i], xi, A[r * p + c]);
+            }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int q = t; q < p * p; q += nt) {
-        const int a = q / p, b = q - a * p;
-        coef[q] = b <= a ? Rinv[(long long)b * p + a] : 0.f;   // (R^-T)[a][b]
-    }
+    for (int a = ty; a < p; a += 16)
+        for (int b = tx; b < p; b += 32) coef[a * p + b] = b <= a ? Rinv[b * p + a] : 0.f;   // (R^-T)[a][b]
 }
 
 // Block-cooperative cyclic Jacobi for a symmetric p x p matrix A (row-major,
@@ -411,13 +439,14 @@ __device__ void block_jacobi(T *A, T *U, int p, T *cs, short *pairs, int max_swe
 // the rows not taken).  An FP32 block carries ~1e-7 relative rounding, so
 // directions far below the largest are noise: taking them would amplify
 // that rounding by s_max / s_i.  work: >= 3 p^2 doubles + p ints.
-__global__ void gram_pivchol_kernel(const double *__restrict__ G, int p, double tol, double *work,
+__global__ void __launch_bounds__(512) gram_pivchol_kernel(const double *__restrict__ G, int p, double tol, double *work,
                                     float *__restrict__ coef, int *__restrict__ r_out, int *__restrict__ flag,
                                     int use_smem)
 {
     extern __shared__ double smem_work[];
     if (use_smem) work = smem_work;
     const int t = threadIdx.x, nt = blockDim.x;
+    const int tx = t & 31, ty = t >> 5;                 // 32 x 16 grid of the trailing updates (512 threads)
     const long long pp = (long long)p * p;
     double *A = work, *R = A + pp, *Ri = R + pp;
     int *piv = reinterpret_cast<int *>(Ri + pp);
@@ -476,29 +505,41 @@ __global__ void gram_pivchol_kernel(const double *__restrict__ G, int p, double 
         }
         __syncthreads();
         if (!s_go) break;
+        // row j of R and the trailing update in one pass (neither touches
+        // row or column piv[j] of A, which both read)
         const int pj = piv[j];
         const double dinv = 1.0 / s_d;
-        for (int k = j + 1 + t; k < p; k += nt) R[(long long)j * p + k] = A[(long long)pj * p + piv[k]] * dinv;
-        __syncthreads();
-        const int m = p - j - 1;
-        for (int q = t; q < m * m; q += nt) {
-            const int kk = j + 1 + q / m, ll = j + 1 + q % m;
-            A[(long long)piv[kk] * p + piv[ll]] -= R[(long long)j * p + kk] * R[(long long)j * p + ll];
+        const double *Aj = A + (long long)pj * p;
+        for (int k = j + 1 + t; k < p; k += nt) R[(long long)j * p + k] = Aj[piv[k]] * dinv;
+        for (int kk = j + 1 + ty; kk < p; kk += 16) {
+            const int pk = piv[kk];
+            const double rk = Aj[pk] * dinv;
+            for (int ll = j + 1 + tx; ll < p; ll += 32) A[(long long)pk * p + piv[ll]] -= rk * (Aj[piv[ll]] * dinv);
         }
         __syncthreads();
     }
     const int r = s_r;
-    // R11^-1 (upper, r x r) by back substitution, one column per thread,
-    // multiplying by the reciprocals of the diagonal (kept in A, free now)
-    for (int i = t; i < r; i += nt) A[i] = 1.0 / R[(long long)i * p + i];
-    __syncthreads();
-    for (int c = t; c < r; c += nt) {
-        for (int i = r - 1; i > c; --i) Ri[(long long)i * r + c] = 0.0;
-        for (int i = c; i >= 0; --i) {
-            double sacc = (i == c) ? 1.0 : 0.0;
-            for (int k = i + 1; k <= c; ++k) sacc -= R[(long long)i * p + k] * Ri[(long long)k * r + c];
-            Ri[(long long)i * r + c] = sacc * A[i];
+    // R11^-1 (upper, r x r) by the column-oriented back substitution, one
+    // barrier per step: at step i row i is final (B[i][c] / R[i][i]) and is
+    // removed from the rows above; B (= I at the start) lives in A, free now
+    for (int a = ty; a < r; a += 16)
+        for (int c = tx; c < r; c += 32) {
+            A[(long long)a * r + c] = a == c ? 1.0 : 0.0;
+            Ri[(long long)a * r + c] = 0.0;            // the strict lower triangle stays zero
         }
+    __syncthreads();
+    for (int i = r - 1; i >= 0; --i) {
+        const double rii = 1.0 / R[(long long)i * p + i];
+        for (int a = ty; a <= i; a += 16)
+            for (int c = tx; c < r; c += 32) {
+                if (c < i) continue;
+                const double xi = A[(long long)i * r + c] * rii;
+                if (a == i)
+                    Ri[(long long)i * r + c] = xi;
+                else
+                    A[(long long)a * r + c] -= R[(long long)a * p + i] * xi;
+            }
+        __syncthreads();
     }
     for (long long q = t; q < (long long)r * p; q += nt) coef[q] = 0.f;
     __syncthreads();
@@ -773,6 +814,19 @@ __global__ void philox_normal_kernel(float *__restrict__ X, long long total, lon
     }
 }
 
+// after the store's work has completed: GBFWI_ETIMEOUT (and the flag
+// cleared) when a product kernel's bounded wait gave up since the last check
+int take_status(gbfwi_bfgs *h)
+{
+    int st = 0;
+    GB_CUDA(cudaMemcpy(&st, h->status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) {
+        GB_CUDA(cudaMemset(h->status.p, 0, sizeof(int)));
+        return GBFWI_ETIMEOUT;
+    }
+    return GBFWI_OK;
+}
+
 int grid_n(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 8); }
 
 // splits of the one- and two-column products
@@ -819,7 +873,7 @@ int atb(gbfwi_bfgs *h, const float *A1, const float *A2, int ka1, int ka, const 
         return GBFWI_OK;
     }
     return gb_tc_atb(A1, A2, ka1, ka, B1, B2, kb1, kb, ld, n, h->part.as<double>(), h->part.bytes / sizeof(double),
-                     out, ldo, s);
+                     out, ldo, h->status.as<int>(), s);
 }
 
 // out[c] = sum_a coef[c][a] row_a + beta * dw * Xc[c], c < nc; rows a < k1
@@ -829,7 +883,7 @@ int combine(gbfwi_bfgs *h, const float *A1, const float *A2, int k1, int ktot, c
 {
     const long long n = h->n, ld = h->ld;
     if (ktot >= 1 && ktot <= 128)
-        return gb_tc_combine(A1, A2, k1, ktot, ld, coef, nc, n, out, ldo, dw, Xc, ldx, beta, s);
+        return gb_tc_combine(A1, A2, k1, ktot, ld, coef, nc, n, out, ldo, dw, Xc, ldx, beta, h->status.as<int>(), s);
     // no rows (out = beta dw Xc) or more than 128: CUDA-core combination
     for (int c0 = 0; c0 < nc; c0 += 64) {
         int cn = std::min(64, nc - c0);
@@ -919,8 +973,8 @@ int apply_dev(gbfwi_bfgs *h, const float *Xd, long long ldx, int p, float *Zd, l
     } else {
         GB_TRY(atb(h, h->S.as<float>(), h->BY.as<float>(), k, 2 * k, Xd, nullptr, p, p, T, p, s));
     }
-    middle_kernel<<<(p + 63) / 64, 64, 0, s>>>(T, h->dSY.as<double>(), h->dYBY.as<double>(), k, h->kmax, p, gamma,
-                                               scr, h->coef.as<float>());
+    middle_kernel<<<p, 32, 0, s>>>(T, h->dSY.as<double>(), h->dYBY.as<double>(), k, h->kmax, p, gamma, scr,
+                                   h->coef.as<float>());
     GB_LAUNCHED();
     return combine(h, h->S.as<float>(), h->BY.as<float>(), k, 2 * k, h->coef.as<float>(), p, Zd, ldz,
                    h->B0.as<float>(), Xd, ldx, beta, s);
@@ -949,12 +1003,13 @@ extern "C" int gbfwi_bfgs_create(long long n, int kmax, const float *B0, gbfwi_b
     if (!rc) rc = h->dSY.ensure((size_t)kmax * kmax * sizeof(double));
     if (!rc) rc = h->dYBY.ensure((size_t)kmax * kmax * sizeof(double));
     if (!rc) rc = h->flag.ensure(16);
+    if (!rc) rc = h->status.ensure(16);
     if (rc) { delete h; return rc; }
     h->SY.assign((size_t)kmax * kmax, 0.0);
     h->YBY.assign((size_t)kmax * kmax, 0.0);
     // the row padding stays zero
     if (cudaMemset(h->S.p, 0, store) != cudaSuccess || cudaMemset(h->Y.p, 0, store) != cudaSuccess ||
-        cudaMemset(h->BY.p, 0, store) != cudaSuccess ||
+        cudaMemset(h->BY.p, 0, store) != cudaSuccess || cudaMemset(h->status.p, 0, 16) != cudaSuccess ||
         cudaMemcpy(h->B0.p, B0, (size_t)n * sizeof(float), cudaMemcpyDefault) != cudaSuccess) {
         gb_set_last_cuda_error(cudaGetLastError(), "initialise the BFGS store", __FILE__, __LINE__);
         delete h;
@@ -1046,6 +1101,7 @@ extern "C" int gbfwi_bfgs_apply(gbfwi_bfgs *h, const float *X, int p, float *Z, 
     if (!dev_out) {
         GB_TRY(unstage_rows(h, Z, Zd, p, s));
         GB_CUDA(cudaStreamSynchronize(s));
+        GB_TRY(take_status(h));
     }
     return GBFWI_OK;
 }
@@ -1102,6 +1158,7 @@ int lowrank_randomized(gbfwi_bfgs *h, const float *X, int p, int rank, unsigned 
     int r = 0;
     GB_CUDA(cudaMemcpyAsync(&r, rdev, sizeof(int), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
+    GB_TRY(take_status(h));
     if (r < 1) return gb_nonfinite("probe block E = (B - B0) X is zero or not finite");
     GB_TRY(combine(h, E, nullptr, p, p, coef, r, Q, ld, nullptr, nullptr, 0, 0.f, s));   // Q1 [r] rows in Q
     // shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa
@@ -1110,7 +1167,7 @@ int lowrank_randomized(gbfwi_bfgs *h, const float *X, int p, int rank, unsigned 
     // adds 1e-5 tr(G) to the diagonal (well above the Gram's rounding), the
     // two unshifted passes make the rows orthonormal to FP32 rounding
     float *Qf = h->V.as<float>();
-    const size_t wc = (size_t)2 * r * r * sizeof(float);
+    const size_t wc = (size_t)3 * r * r * sizeof(float);
     const int chol_smem = wc <= 200 * 1024;
     if (chol_smem) GB_CUDA(cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wc));
     for (int pass = 0; pass < 3; ++pass) {
@@ -1163,6 +1220,7 @@ int lowrank_randomized(gbfwi_bfgs *h, const float *X, int p, int rank, unsigned 
     int flag_h = 0;
     GB_CUDA(cudaMemcpyAsync(&flag_h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
+    GB_TRY(take_status(h));
     if (flag_h) {
         static const char *stage[] = {"", "Gram matrix of E", "Cholesky pivot of the basis Gram matrix",
                                       "singular Q^T X", "eigenvalues of Omega"};
@@ -1232,12 +1290,13 @@ extern "C" int gbfwi_lowrank_exact(gbfwi_bfgs *h, int rank, double eps_prior, fl
     int r = 0;
     GB_CUDA(cudaMemcpyAsync(&r, rdev, sizeof(int), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
+    GB_TRY(take_status(h));
     if (r < 1) return gb_nonfinite("BFGS pairs S, B0 Y are zero or not finite");
     coef_colscale_kernel<<<grid_n((long long)r * m), 256, 0, s>>>(coef, r, m, d);
     GB_LAUNCHED();
     float *Qa = h->E.as<float>(), *Qb = h->Q.as<float>();
     GB_TRY(combine(h, S, BY, k, m, coef, r, Qa, ld, nullptr, nullptr, 0, 0.f, s));
-    const size_t wc = (size_t)2 * r * r * sizeof(float);
+    const size_t wc = (size_t)3 * r * r * sizeof(float);
     const int chol_smem = wc <= 200 * 1024;
     if (chol_smem) GB_CUDA(cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wc));
     for (int pass = 0; pass < 3; ++pass) {   // shifted CholeskyQR3, as in gbfwi_lowrank_invhess
@@ -1307,6 +1366,7 @@ extern "C" int gbfwi_lowrank_exact(gbfwi_bfgs *h, int rank, double eps_prior, fl
     int flag_h = 0;
     GB_CUDA(cudaMemcpyAsync(&flag_h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
+    GB_TRY(take_status(h));
     if (flag_h) return gb_nonfinite("exact low-rank decomposition of the BFGS pairs");
     return GBFWI_OK;
 }

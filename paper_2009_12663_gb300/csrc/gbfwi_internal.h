@@ -222,17 +222,20 @@ int gb_prepare_step(int mode, int tile);   // set kernel attributes outside any 
 // small kernels of the SEM driver
 int gb_material(gbfwi_mesh *m, cudaStream_t s);
 
-// tensor-core (3xTF32) products of the BFGS / randomized-SVD blocks
+// tensor-core products of the BFGS / randomized-SVD blocks
 // (tc_products.cu).  Rows are length-n FP32 vectors with row stride ld (a
-// multiple of 4; rows 16-byte aligned); an operand of ka rows takes rows
-// a < ka1 from A1 and the rest from A2 (likewise B).
+// multiple of 64 floats; rows 256-byte aligned, readable up to the pitch);
+// an operand of ka rows takes rows a < ka1 from A1 and the rest from A2
+// (likewise B).
 //   out[a][b] (FP64, row stride ldo) = sum_i A_a[i] B_b[i], through
-//   gb_tc_atb_splits(ka, kb, n) * ka * kb doubles of split-K partials;
-//   out[c][i] = sum_a coef[c][a] R_a[i] + beta dw[i] Xc[c][i] (ktot <= 128).
+//   gb_tc_atb_splits(ka, kb, n) * ka * kb doubles of split-K partials
+//   (tcgen05; *status set to 1 when a bounded wait gave up);
+//   out[c][i] = sum_a coef[c][a] R_a[i] + beta dw[i] Xc[c][i] (ktot <= 128;
+//   tcgen05, same status flag).
 long long gb_tc_atb_splits(int ka, int kb, long long n);
 int gb_tc_atb(const float *A1, const float *A2, int ka1, int ka, const float *B1, const float *B2, int kb1, int kb,
               long long ld, long long n, double *part, size_t part_doubles, double *out, long long ldo,
-              cudaStream_t s);
+              int *status, cudaStream_t s);
 int gb_tc_combine(const float *R1, const float *R2, int k1, int ktot, long long ldr, const float *coef, int nc,
                   long long n, float *out, long long ldo, const float *dw, const float *Xc, long long ldx,
-                  float beta, cudaStream_t s);
+                  float beta, int *status, cudaStream_t s);

@@ -33,6 +33,12 @@
 // in four colour passes (sem_pc_step_kernel).
 
 #include "gbfwi_internal.h"
+#include "sm100.h"
+
+using sm100::bulk_g2s;
+using sm100::mbar_arrive_expect_tx;
+using sm100::mbar_init;
+using sm100::mbar_wait_bounded;
 
 __constant__ float cD[GB_NG * GB_NG];   // D[i*5+k] = l_k'(xi_i)
 __constant__ float cW[GB_NG * GB_NG];   // w_i w_j at [j*5+i]
@@ -305,58 +311,6 @@ struct StepShape {
     static constexpr int MINB = ((MODE == MODE_FWD ? 512 : 384) / NT) > 0 ? (MODE == MODE_FWD ? 512 : 384) / NT : 1;
     static constexpr size_t bytes = (size_t)NWIN * WIN * sizeof(float2) + NZB * ZB + VB;
 };
-
-// ---------------------------------------------------------------------------
-// bulk asynchronous copies (TMA unit) completing on a shared-memory mbarrier
-// ---------------------------------------------------------------------------
-
-// bound of a device-side wait: about one second at the SM clock
-constexpr long long kWaitCycles = 2000000000LL;
-
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long *mbar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// the calling thread's arrival, announcing `bytes` of copies
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *mbar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
-                 : "memory");
-}
-
-// global -> shared copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *mbar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(mbar))
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *mbar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(mbar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// wait for phase `parity` of the barrier; false when the bound ran out
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *mbar, unsigned parity)
-{
-    if (mbar_try_wait(mbar, parity)) return true;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(mbar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
-    return true;
-}
 
 // x-step of the assembly: v(0, j) += left neighbour's v(4, j) (lane - 1)
 __device__ __forceinline__ void assemble_x(float2 (&v)[25], bool has_left)

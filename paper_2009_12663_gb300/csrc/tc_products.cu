@@ -7,27 +7,35 @@
 // Precision.  Every operand is FP32.  Each value x is split exactly into
 // three bfloat16 parts, x = x1 + x2 + x3 (x1 = bf16(x), x2 = bf16(x - x1),
 // x3 = x - x1 - x2: 8 significant bits each, 24 in all), and a product is
-// taken as the six terms x_i y_j with i + j <= 4 on the tensor cores
-// (mma.sync m16n8k16 BF16, products exact in the FP32 accumulator), small
+// taken as the six terms x_i y_j with i + j <= 4 on the tensor cores, small
 // terms first; the dropped x2 y3, x3 y2, x3 y3 are below 2^-23 of |x y|, so a
 // product is as accurate as an FP32 product (the splitting of Ootomo &
 // Yokota (2022) carried to three bfloat16 parts, which is exact where two
-// TF32 parts are not).  The tensor core's FP32 accumulation is kept short:
-// after every 16-deep K step its sum is folded into a compensated FP32 pair
-// (TwoSum of Knuth), so the long sums over n of the split-K products are
-// close to exact sums of the FP32 products, and the splits are reduced in
-// FP64; the row combinations sum at most 128 terms the same way.  (A probe
-// of mma.sync on sm_103a: a BF16 or TF32 MMA keeps about 24 bits below its
-// largest term and truncates the rest.)
+// TF32 parts are not).  The tensor core keeps about 24 bits below the largest
+// term of an MMA and truncates the rest (measured on sm_103a for mma.sync and
+// for tcgen05.mma), so its accumulation never spans more than one 16-deep K
+// step: each step's six part products go into a fresh TMEM accumulator, the
+// step sums are added in FP32, and the long sums over n of the split-K
+// products are carried in compensated FP32 pairs (TwoSum of Knuth) and
+// reduced over the splits in FP64.
 //
-// Layout: rows are vectors of length n with a row stride ld (a multiple of
-// 4 floats, rows 16-byte aligned); both kernels stage their operands in
-// shared memory with 16-byte cp.async copies (zero-filled beyond n and
-// beyond the last row).
+// Machinery (sm_100 family, inline PTX in sm100.h): operands arrive in
+// shared memory by 2-D tensor-map loads (cp.async.bulk.tensor, zero past n)
+// or one bulk copy per row, completing on mbarriers; the split parts are
+// written into K-major 128-byte-swizzled planes read by tcgen05.mma (one
+// issuing thread, accumulators in tensor memory), whose completion is
+// committed to an mbarrier; the accumulators come back with tcgen05.ld.
+// Rows are vectors of length n with a row stride ld (a multiple of 64
+// floats, rows 256-byte aligned, readable up to the pitch).
 
 #include <algorithm>
+#include <cstring>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "gbfwi_internal.h"
+#include "sm100.h"
 
 namespace {
 
@@ -53,35 +61,6 @@ __device__ __forceinline__ void split3(float u, float v, unsigned (&p)[3])
     p[2] = pack_bf16(ur2, vr2);
 }
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
-                                         unsigned b0, unsigned b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};\n"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// d += the six terms a_i b_j, i + j <= 4 (parts 0..2), smallest first
-__device__ __forceinline__ void mma_split6(float (&d)[4], const unsigned (&a)[3][4], const unsigned (&b)[3][2])
-{
-    mma_bf16(d, a[2][0], a[2][1], a[2][2], a[2][3], b[0][0], b[0][1]);
-    mma_bf16(d, a[0][0], a[0][1], a[0][2], a[0][3], b[2][0], b[2][1]);
-    mma_bf16(d, a[1][0], a[1][1], a[1][2], a[1][3], b[1][0], b[1][1]);
-    mma_bf16(d, a[1][0], a[1][1], a[1][2], a[1][3], b[0][0], b[0][1]);
-    mma_bf16(d, a[0][0], a[0][1], a[0][2], a[0][3], b[1][0], b[1][1]);
-    mma_bf16(d, a[0][0], a[0][1], a[0][2], a[0][3], b[0][0], b[0][1]);
-}
-
-__device__ __forceinline__ void cp16(void *smem, const void *gmem, int src_bytes)
-{
-    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
 // s + e += x, keeping s + e exact up to the rounding of e (TwoSum)
 __device__ __forceinline__ void two_sum_add(float &s, float &e, float x)
 {
@@ -99,143 +78,229 @@ __device__ __forceinline__ const float *row_of(const float *P1, const float *P2,
 }
 
 // ---------------------------------------------------------------------------
-// split-K product: part[sx][a][b] = sum_{i in split sx} A_a[i] B_b[i]
-// CTA: 64 x 64 output tile, 4 warps of 32 x 32 (2 m16 x 4 n8 MMA tiles);
-// K staged 32 at a time (two 16-deep MMA steps) through a double-buffered
-// cp.async pipeline; every staged element is split into its three bfloat16
-// parts once, into shared planes the fragments are read from.
-// grid (ceil(kb / 64), ceil(ka / 64), nsplit): the splits vary slowest, so
-// the tiles that read the same K range run together and share it in L2.
+// split-K product on the 5th-generation tensor cores (tcgen05):
+// part[sx][p sp + q sq] = sum_{i in split sx} P_p[i] Q_q[i]
+// CTA tile: 128 P rows (the MMA's M, accumulator lane) x 64 Q rows (N);
+// K steps of 64 through a two-stage ring of raw FP32 rows filled by bulk
+// copies (one 256-byte row per copy, completing on an mbarrier).  Every
+// staged element is split once into its three bfloat16 parts, written into
+// three K-major 128-byte-swizzled planes per operand; per 16-deep K step one
+// thread issues the six part products (smallest first) into a fresh TMEM
+// accumulator (M 128, N 64), four steps per stage into four accumulators;
+// the accumulator set of the previous stage is added in FP32 and folded into
+// compensated FP32 pairs (TwoSum) while the tensor core works on the current
+// one.  Two
+// accumulator sets of 4 x 64 columns fill the 512 TMEM columns (one CTA per
+// SM).  Elements at i >= n are taken as zero (rows are read to the 64-float
+// row pitch).
 // ---------------------------------------------------------------------------
 
-// row pitches: raw FP32 tiles 32 floats (16-byte cp.async rows), split
-// planes 20 words (the fragment loads of a warp hit 32 distinct banks)
-constexpr int AT_M = 64, AT_N = 64, AT_K = 32, AT_P = AT_K, AT_PP = AT_K / 2 + 4, AT_THREADS = 128;
-constexpr size_t AT_RAW = (size_t)(AT_M + AT_N) * AT_P;          // floats of one raw stage
-constexpr size_t AT_PLANE = (size_t)(AT_M + AT_N) * AT_PP;       // words of one split plane
-constexpr size_t AT_SMEM = (2 * AT_RAW + 3 * AT_PLANE) * sizeof(float);
+constexpr int T5_M = 128, T5_N = 64, T5_K = 64, T5_THREADS = 256;
+constexpr size_t T5_PLANE_P = (size_t)T5_M * 128;                 // bytes of one bfloat16 part plane of P
+constexpr size_t T5_PLANE_Q = (size_t)T5_N * 128;
+constexpr size_t T5_RAW = (size_t)(T5_M + T5_N) * T5_K * sizeof(float);   // one raw FP32 stage
+constexpr size_t T5_SMEM = 1024 + 3 * (T5_PLANE_P + T5_PLANE_Q) + 2 * T5_RAW;
 
-__global__ void __launch_bounds__(AT_THREADS, 3) atb_tc_kernel(const float *__restrict__ A1, const float *__restrict__ A2,
-                                                            int ka1, int ka, const float *__restrict__ B1,
-                                                            const float *__restrict__ B2, int kb1, int kb,
-                                                            long long ld, long long n, long long chunk,
-                                                            double *__restrict__ part)
+// 2-D tensor maps of the operand row blocks for single-tile products (P at
+// most 128 rows, Q at most 64): map b covers rows [0, h[b]) of its block,
+// landing at raw rows off[b]; elements at i >= n are filled with zeros
+struct Tc05Maps {
+    CUtensorMap m[4];    // P1, P2, Q1, Q2
+    int h[4];            // box rows (0: block absent)
+    int off[4];
+    int use;             // 1: tensor-map loads, 0: one bulk copy per row
+};
+
+__global__ void __launch_bounds__(T5_THREADS, 1)
+    atb_tc05_kernel(const __grid_constant__ Tc05Maps maps, const float *__restrict__ P1, const float *__restrict__ P2, int kp1, int kp,
+                    const float *__restrict__ Q1, const float *__restrict__ Q2, int kq1, int kq, long long ld,
+                    long long n, long long chunk, double *__restrict__ part, long long split_stride, long long sp,
+                    long long sq, int *__restrict__ status)
 {
-    extern __shared__ float4 at_smem4[];
-    float *raw = reinterpret_cast<float *>(at_smem4);                  // [2][128 rows][32]
-    unsigned *pl = reinterpret_cast<unsigned *>(raw + 2 * AT_RAW);     // [3][128 rows][20]
+    using namespace sm100;
+    extern __shared__ unsigned char t5_smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)t5_smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *planeP = base;                                   // [3][128 rows][128 B]
+    unsigned char *planeQ = base + 3 * T5_PLANE_P;                  // [3][64 rows][128 B]
+    float *raw = reinterpret_cast<float *>(planeQ + 3 * T5_PLANE_Q);   // [2][192 rows][64]
+    __shared__ unsigned long long mbar_raw[2], mbar_mma[2];
+    __shared__ unsigned tslot;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int sx = blockIdx.z;
-    const int a0 = blockIdx.y * AT_M, b0 = blockIdx.x * AT_N;
+    const int p0 = blockIdx.y * T5_M, q0 = blockIdx.x * T5_N;
+    const int np = min(T5_M, kp - p0), nq = min(T5_N, kq - q0);
     const long long ib = (long long)sx * chunk;
     const long long ie = min(n, ib + chunk);
-    const int nk = (int)((ie - ib + AT_K - 1) / AT_K);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
+    const int nk = (int)((ie - ib + T5_K - 1) / T5_K);
 
-    // raw stage: rows 0..63 of A then 0..63 of B, 8 16-byte chunks each
-    auto load = [&](int buf, int kt) {
-        float *dst = raw + (size_t)buf * AT_RAW;
-        const long long i0 = ib + (long long)kt * AT_K;
+    if (warp == 0) tmem_alloc(&tslot, 512);
+    if (tid == 0) {
+        mbar_init(&mbar_raw[0], 1);
+        mbar_init(&mbar_raw[1], 1);
+        mbar_init(&mbar_mma[0], 1);
+        mbar_init(&mbar_mma[1], 1);
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const unsigned tbase = tslot;
+
+    // stage kt: P rows to raw rows [0, np), Q rows to [128, 128 + nq), by up to
+    // four tensor-map loads or one bulk copy per row
+    auto issue = [&](int kt) {
+        float *buf = raw + (size_t)(kt & 1) * (T5_M + T5_N) * T5_K;
+        const long long i0 = ib + (long long)kt * T5_K;
+        if (maps.use) {
+            if (tid == 0) {
+                mbar_arrive_expect_tx(&mbar_raw[kt & 1],
+                                      (unsigned)(maps.h[0] + maps.h[1] + maps.h[2] + maps.h[3]) * T5_K * sizeof(float));
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int q = tid + u * AT_THREADS;           // 0..1023
-            const int r = q >> 3, c = q & 7;               // r: 0..127
-            const bool isb = r >= 64;
-            const int row = (isb ? b0 - 64 : a0) + r;
-            const int lim = isb ? kb : ka;
-            const long long i = i0 + 4 * c;
-            int bytes = 0;
-            const float *src = isb ? B1 : A1;
-            if (row < lim && i < ie) {
-                src = isb ? row_of(B1, B2, kb1, row, ld) + i : row_of(A1, A2, ka1, row, ld) + i;
-                bytes = (int)min(16LL, (ie - i) * 4);
+                for (int b = 0; b < 4; ++b)
+                    if (maps.h[b] > 0) tma_load_2d(buf + (size_t)maps.off[b] * T5_K, &maps.m[b], (int)i0, 0, &mbar_raw[kt & 1]);
             }
-            cp16(dst + r * AT_P + 4 * c, src, bytes);
+            return;
+        }
+        if (tid == 0) mbar_arrive_expect_tx(&mbar_raw[kt & 1], (unsigned)(np + nq) * T5_K * sizeof(float));
+        for (int r = tid; r < np + nq; r += T5_THREADS) {
+            const bool isp = r < np;
+            const float *src = isp ? row_of(P1, P2, kp1, p0 + r, ld) + i0 : row_of(Q1, Q2, kq1, q0 + r - np, ld) + i0;
+            float *dst = buf + (size_t)(isp ? r : T5_M + r - np) * T5_K;
+            bulk_g2s(dst, src, T5_K * sizeof(float), &mbar_raw[kt & 1]);
+        }
+    };
+    issue(0);
+    if (nk > 1) issue(1);
+
+    constexpr unsigned idesc = idesc_bf16_f32(T5_M, T5_N);
+    const int m = 32 * (warp & 3) + lane;                // accumulator row (TMEM lane) of this thread
+    const int c0 = 32 * (warp >> 2);                     // its 32 of the 64 accumulator columns
+    const unsigned tl = tbase + ((unsigned)(32 * (warp & 3)) << 16);
+    float S[32], E[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) S[j] = E[j] = 0.f;
+
+    // fold accumulator set `set` into the compensated pairs: the four 16-deep
+    // step sums (each from a fresh accumulator, so the tensor core's
+    // truncation never spans more than one step) are added in FP32 and the
+    // result folded by TwoSum; warps whose 32 rows are all beyond np skip it
+    const bool folds = 32 * (warp & 3) < np;
+    auto fold = [&](int set) {
+        if (!folds) return;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[4][16];
+            const unsigned tc = tl + set * 256 + c0 + 16 * h;
+            tmem_ld16x4(tc, tc + 64, tc + 128, tc + 192, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                two_sum_add(S[16 * h + j], E[16 * h + j], (v[0][j] + v[1][j]) + (v[2][j] + v[3][j]));
         }
     };
 
-    float S[2][4][4], E[2][4][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) S[mt][nt][v] = E[mt][nt][v] = 0.f;
-
-    load(0, 0);
-    cp_commit();
-    if (nk > 1) load(1, 1);
-    cp_commit();
+    bool ok = true;
+    int kfail = nk;                                      // first stage whose wait gave up
     for (int kt = 0; kt < nk; ++kt) {
-        cp_wait<1>();
-        __syncthreads();                                   // raw stage kt landed; planes free
+        // stage kt landed; the MMAs of stage kt - 1 have released the planes
+        // (each thread waits itself; a bound that ran out is agreed on at the
+        // barrier below, before anything reads what was written)
+        bool w = mbar_wait_bounded(&mbar_raw[kt & 1], (kt >> 1) & 1);
+        if (kt > 0) w = w && mbar_wait_bounded(&mbar_mma[(kt - 1) & 1], ((kt - 1) >> 1) & 1);
+        fence_after_sync();
+        // split: the np + nq present rows x 8 chunks of 8 elements, each into
+        // three 16-byte part chunks (elements at i >= ie zeroed in the last stage)
         {
-            // split every element of the stage once: 128 rows x 16 pairs
-            const float *src = raw + (size_t)(kt & 1) * AT_RAW;
+            const float *src = raw + (size_t)(kt & 1) * (T5_M + T5_N) * T5_K;
+            const long long i0 = ib + (long long)kt * T5_K;
+            const bool tail = i0 + T5_K > ie;
+            for (int item = tid; item < 8 * (np + nq); item += T5_THREADS) {
+                const int rr0 = item >> 3, c = item & 7;
+                const bool isp = rr0 < np;
+                const int rr = isp ? rr0 : rr0 - np;
+                const float *row = src + (size_t)(isp ? rr : T5_M + rr) * T5_K + 8 * c;
+                const float4 x0 = *reinterpret_cast<const float4 *>(row);
+                const float4 x1 = *reinterpret_cast<const float4 *>(row + 4);
+                float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                if (tail) {
+                    const long long ic = i0 + 8 * c;
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int q = tid + u * AT_THREADS;        // 0..2047
-                const int r = q >> 4, c = q & 15;
-                const float2 v = *reinterpret_cast<const float2 *>(src + r * AT_P + 2 * c);
-                unsigned s3[3];
-                split3(v.x, v.y, s3);
+                    for (int e = 0; e < 8; ++e)
+                        if (ic + e >= ie) x[e] = 0.f;
+                }
+                unsigned pr[3][4];
 #pragma unroll
-                for (int part = 0; part < 3; ++part) pl[part * AT_PLANE + r * AT_PP + c] = s3[part];
+                for (int h = 0; h < 4; ++h) {
+                    unsigned s3[3];
+                    split3(x[2 * h], x[2 * h + 1], s3);
+                    pr[0][h] = s3[0];
+                    pr[1][h] = s3[1];
+                    pr[2][h] = s3[2];
+                }
+                unsigned char *pl = isp ? planeP : planeQ;
+                const size_t pstride = isp ? T5_PLANE_P : T5_PLANE_Q;
+                const unsigned off = k128_offset(rr, 8 * c);
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    *reinterpret_cast<uint4 *>(pl + q * pstride + off) = make_uint4(pr[q][0], pr[q][1], pr[q][2], pr[q][3]);
             }
         }
-        __syncthreads();                                   // planes ready; raw stage kt free
-        if (kt + 2 < nk) load(kt & 1, kt + 2);
-        cp_commit();
+        fence_async_smem();
+        fence_before_sync();
+        if (__syncthreads_or(!w)) {                      // planes ready; raw stage kt & 1 free
+            ok = false;
+            kfail = kt;
+            break;
+        }
+        if (kt + 2 < nk) issue(kt + 2);
+        if (tid == 0) {
+            fence_after_sync();
+            const unsigned dset = tbase + (unsigned)((kt & 1) * 256);
 #pragma unroll
-        for (int kk = 0; kk < AT_K; kk += 16) {
-            unsigned a[2][3][4], b[4][3][2];
-            const int kw = kk / 2 + t;                     // word of the pair (kk + 2t, kk + 2t + 1)
+            for (int kk = 0; kk < 4; ++kk) {
+                unsigned long long a[3], b[3];
 #pragma unroll
-            for (int part = 0; part < 3; ++part) {
-                const unsigned *P = pl + part * AT_PLANE;
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    const int r = wm + mt * 16 + g;
-                    a[mt][part][0] = P[r * AT_PP + kw];
-                    a[mt][part][1] = P[(r + 8) * AT_PP + kw];
-                    a[mt][part][2] = P[r * AT_PP + kw + 4];
-                    a[mt][part][3] = P[(r + 8) * AT_PP + kw + 4];
+                for (int q = 0; q < 3; ++q) {
+                    a[q] = sdesc_k128(planeP + q * T5_PLANE_P) + 2 * kk;
+                    b[q] = sdesc_k128(planeQ + q * T5_PLANE_Q) + 2 * kk;
                 }
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) {
-                    const int r = 64 + wn + nt * 8 + g;
-                    b[nt][part][0] = P[r * AT_PP + kw];
-                    b[nt][part][1] = P[r * AT_PP + kw + 4];
-                }
+                const unsigned d = dset + kk * 64;
+                // the six terms a_i b_j, i + j <= 2 (parts 0 largest), smallest first
+                sm100::mma_bf16(d, a[2], b[0], idesc, false);
+                sm100::mma_bf16(d, a[0], b[2], idesc, true);
+                sm100::mma_bf16(d, a[1], b[1], idesc, true);
+                sm100::mma_bf16(d, a[1], b[0], idesc, true);
+                sm100::mma_bf16(d, a[0], b[1], idesc, true);
+                sm100::mma_bf16(d, a[0], b[0], idesc, true);
             }
-            // each 16-product sum goes into the compensated pair at once:
-            // the tensor core truncates its FP32 sums, and a longer run in
-            // its accumulator measurably biases the small directions of an
-            // ill-conditioned block
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) {
-                    float D[4] = {0.f, 0.f, 0.f, 0.f};
-                    mma_split6(D, a[mt], b[nt]);
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) two_sum_add(S[mt][nt][v], E[mt][nt][v], D[v]);
-                }
+            mma_commit(&mbar_mma[kt & 1]);
+        }
+        if (kt > 0) fold((kt - 1) & 1);                  // overlaps the MMAs of stage kt
+    }
+    if (ok && nk > 0) {
+        ok = __syncthreads_and(mbar_wait_bounded(&mbar_mma[(nk - 1) & 1], ((nk - 1) >> 1) & 1));
+        if (!ok) kfail = nk;
+        if (ok) {
+            fence_after_sync();
+            fold((nk - 1) & 1);
         }
     }
-    cp_wait<0>();
+    if (ok) {
+        if (m < np) {
+            double *dst = part + (long long)sx * split_stride + (long long)(p0 + m) * sp;
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int a = a0 + wm + mt * 16 + g + ((v & 2) ? 8 : 0);
-                const int b = b0 + wn + nt * 8 + 2 * t + (v & 1);
-                if (a < ka && b < kb)
-                    part[((long long)sx * ka + a) * kb + b] = (double)S[mt][nt][v] + (double)E[mt][nt][v];
-            }
+            for (int j = 0; j < 32; ++j)
+                if (c0 + j < nq) dst[(long long)(q0 + c0 + j) * sq] = (double)S[j] + (double)E[j];
+        }
+    } else {
+        if (tid == 0 && status) atomicExch(status, 1);
+        // give the copies and MMAs still in flight a bounded wait before the
+        // shared memory and the accumulators are released
+        for (int st = kfail; st < min(nk, kfail + 2); ++st) mbar_wait_bounded(&mbar_raw[st & 1], (st >> 1) & 1);
+        if (kfail > 0) mbar_wait_bounded(&mbar_mma[(kfail - 1) & 1], ((kfail - 1) >> 1) & 1);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tbase, 512);
 }
 
 __global__ void split_reduce_kernel(const double *__restrict__ part, int nsplit, int ka, int kb,
@@ -250,245 +315,364 @@ __global__ void split_reduce_kernel(const double *__restrict__ part, int nsplit,
 }
 
 // ---------------------------------------------------------------------------
-// row combination: out[c][i] = sum_a coef[c][a] R_a[i] + beta dw[i] Xc[c][i]
-// for c in [c0, c0 + 16 MT) (blockIdx.y selects c0 = 64 blockIdx.y).
-// coef stays in shared memory, split once; persistent CTAs walk over
-// 64-column tiles, streaming R in K steps of 32 rows (two 16-deep MMA steps)
-// through a four-stage cp.async pipeline.  4 warps, each all MT m16 tiles x
-// 2 n8 tiles (16 columns).  The sums over K (at most 128 terms) are folded
-// into compensated FP32 pairs after every 16-deep step, as in the split-K
-// product: the basis combinations of the randomized SVD have ill-conditioned
-// coefficients, and a plain FP32 sum of their terms loses the small
-// directions.
+// row combination on the 5th-generation tensor cores (tcgen05):
+// out[c][i] = sum_a coef[c][a] R_a[i] + beta dw[i] Xc[c][i], c in
+// [64 blockIdx.y, + 64), a < ktot <= 128.  The MMA's M is a tile of 128
+// columns i, N the 64 outputs c, K the rows a: persistent CTAs walk over the
+// column tiles; a tile's rows arrive by tensor-map loads (one per row block,
+// zero past n) or one bulk copy per row, are split into three bfloat16 parts
+// and transposed into K-major 128-byte-swizzled planes (two 64-row K
+// blocks); coef is split once per CTA.  Per 16-row K step one thread issues
+// the six part products into a fresh TMEM accumulator (up to 8 x 64
+// columns); the step sums are added pairwise in FP32.
 // ---------------------------------------------------------------------------
 
-// R stages are raw FP32 [32 rows][64 columns]; each stage is split once into
-// three planes of row pairs [16][72 words] (conflict-free fragment loads);
-// coef is split once into three planes [16 MT][K/2 + 4 words].
-constexpr int CB_N = 64, CB_K = 32, CB_RPP = CB_N + 8, CB_STAGES = 4, CB_THREADS = 128;
-constexpr size_t CB_RAW = (size_t)CB_K * CB_N;            // floats of one raw stage
-constexpr size_t CB_PLANE = (size_t)(CB_K / 2) * CB_RPP;  // words of one split plane of R
+constexpr int C5_M = 128, C5_N = 64, C5_KB = 64, C5_THREADS = 256;
+constexpr size_t C5_APLANE = (size_t)C5_M * 128;                 // bytes of one A part plane (one K block)
+constexpr size_t C5_BPLANE = (size_t)C5_N * 128;
+constexpr size_t C5_RAW = (size_t)128 * C5_M * sizeof(float);    // rows a x 128 columns
+constexpr size_t C5_SMEM = 1024 + 6 * C5_APLANE + 6 * C5_BPLANE + C5_RAW;
 
-template <int MT>
-__global__ void __launch_bounds__(CB_THREADS) combine_tc_kernel(const float *__restrict__ R1,
-                                                                const float *__restrict__ R2, int k1, int ktot,
-                                                                long long ldr, const float *__restrict__ coef,
-                                                                int nc, long long n, float *__restrict__ out,
-                                                                long long ldo, const float *__restrict__ dw,
-                                                                const float *__restrict__ Xc, long long ldx,
-                                                                float beta)
+struct Cb5Maps {
+    CUtensorMap m[2];    // R1, R2
+    int h[2];            // box rows (0: block absent)
+    int use;
+};
+
+__global__ void __launch_bounds__(C5_THREADS, 1)
+    combine_tc05_kernel(const __grid_constant__ Cb5Maps maps, const float *__restrict__ R1,
+                        const float *__restrict__ R2, int k1, int ktot, long long ldr, const float *__restrict__ coef,
+                        int nc, long long n, float *__restrict__ out, long long ldo, const float *__restrict__ dw,
+                        const float *__restrict__ Xc, long long ldx, float beta, int *__restrict__ status)
 {
-    extern __shared__ float4 cb_smem4[];
-    const int kp = (ktot + CB_K - 1) / CB_K * CB_K;      // K padded to whole steps
-    const int cpp = kp / 2 + 4;                          // coef plane pitch in words
-    float *raw = reinterpret_cast<float *>(cb_smem4);                   // [stages][32][64]
-    unsigned *rp = reinterpret_cast<unsigned *>(raw + CB_STAGES * CB_RAW);   // [3][16][72]
-    unsigned *cp = rp + 3 * CB_PLANE;                                   // [3][16 MT][cpp]
-    const int c0 = blockIdx.y * 64;
+    using namespace sm100;
+    extern __shared__ unsigned char c5_smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)c5_smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *planeA = base;                                  // [kb 2][part 3][128 rows i][128 B]
+    unsigned char *planeB = base + 6 * C5_APLANE;                  // [kb 2][part 3][64 rows c][128 B]
+    float *raw = reinterpret_cast<float *>(planeB + 6 * C5_BPLANE);   // [ktot rows a][128]
+    __shared__ unsigned long long mbar_raw, mbar_mma;
+    __shared__ unsigned tslot;
+
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int wn = warp * 16;
-    // coef planes: pairs along K of each output row
-    for (int q = tid; q < 16 * MT * (kp / 2); q += CB_THREADS) {
-        const int c = q / (kp / 2), w = q - c * (kp / 2);
-        const int a = 2 * w;
-        const bool ok = c0 + c < nc;
-        const float u = (ok && a < ktot) ? coef[(long long)(c0 + c) * ktot + a] : 0.f;
-        const float v = (ok && a + 1 < ktot) ? coef[(long long)(c0 + c) * ktot + a + 1] : 0.f;
-        unsigned s3[3];
-        split3(u, v, s3);
-#pragma unroll
-        for (int part = 0; part < 3; ++part) cp[(size_t)part * 16 * MT * cpp + c * cpp + w] = s3[part];
+    const int c0 = blockIdx.y * C5_N;
+    const int ncl = min(C5_N, nc - c0);
+    const int nks = (ktot + 15) / 16;                    // 16-row K steps
+    const long long ntiles = (n + C5_M - 1) / C5_M;
+
+    if (warp == 0) tmem_alloc(&tslot, 512);
+    if (tid == 0) {
+        mbar_init(&mbar_raw, 1);
+        mbar_init(&mbar_mma, 1);
     }
-    const long long ntiles = (n + CB_N - 1) / CB_N;
-    const int nks = kp / CB_K;
-    const long long my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const long long total = my_tiles * nks;
-    auto load = [&](long long f) {
-        const long long tile = blockIdx.x + (f / nks) * gridDim.x;
-        const int ks = (int)(f % nks);
-        float *dst = raw + (size_t)(f % CB_STAGES) * CB_RAW;
-        const long long i0 = tile * CB_N;
+    // coef split once: B[c][a], zero beyond ncl rows and ktot columns
+    for (int item = tid; item < C5_N * 16; item += C5_THREADS) {
+        const int c = item >> 4, q = item & 15;          // 16 chunks of 8 along a (two K blocks)
+        float x[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {                     // 32 rows x 16 chunks = 512 chunks
-            const int q = tid + u * CB_THREADS;
-            const int r = q >> 4, c = q & 15;
-            const int a = ks * CB_K + r;
-            const long long i = i0 + 4 * c;
-            int bytes = 0;
-            const float *src = R1 ? R1 : R2;
-            if (a < ktot && i < n) {
-                src = row_of(R1, R2, k1, a, ldr) + i;
-                bytes = (int)min(16LL, (n - i) * 4);
-            }
-            cp16(dst + r * CB_N + 4 * c, src, bytes);
+        for (int e = 0; e < 8; ++e) {
+            const int a = 8 * q + e;
+            x[e] = (c < ncl && a < ktot) ? coef[(long long)(c0 + c) * ktot + a] : 0.f;
         }
+        unsigned pr[3][4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            unsigned s3[3];
+            split3(x[2 * h], x[2 * h + 1], s3);
+            pr[0][h] = s3[0];
+            pr[1][h] = s3[1];
+            pr[2][h] = s3[2];
+        }
+        const int kb = q >> 3;
+        const unsigned off = k128_offset(c, 8 * (q & 7));
+#pragma unroll
+        for (int pt = 0; pt < 3; ++pt)
+            *reinterpret_cast<uint4 *>(planeB + (kb * 3 + pt) * C5_BPLANE + off) =
+                make_uint4(pr[pt][0], pr[pt][1], pr[pt][2], pr[pt][3]);
+    }
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const unsigned tbase = tslot;
+
+    auto issue = [&](long long tile) {
+        const long long i0 = tile * C5_M;
+        if (maps.use) {
+            if (tid == 0) {
+                mbar_arrive_expect_tx(&mbar_raw, (unsigned)(maps.h[0] + maps.h[1]) * C5_M * sizeof(float));
+                if (maps.h[0] > 0) tma_load_2d(raw, &maps.m[0], (int)i0, 0, &mbar_raw);
+                if (maps.h[1] > 0) tma_load_2d(raw + (size_t)maps.h[0] * C5_M, &maps.m[1], (int)i0, 0, &mbar_raw);
+            }
+            return;
+        }
+        const long long iend = min(i0 + C5_M, ldr);      // rows are readable to their pitch
+        const unsigned bytes = (unsigned)(iend - i0) * sizeof(float);
+        if (tid == 0) mbar_arrive_expect_tx(&mbar_raw, (unsigned)ktot * bytes);
+        for (int a = tid; a < ktot; a += C5_THREADS)
+            bulk_g2s(raw + (size_t)a * C5_M, row_of(R1, R2, k1, a, ldr) + i0, bytes, &mbar_raw);
     };
-    for (long long f = 0; f < CB_STAGES - 1; ++f) {
-        if (f < total) load(f);
-        cp_commit();
+
+    constexpr unsigned idesc = idesc_bf16_f32(C5_M, C5_N);
+    const int i_loc = 32 * (warp & 3) + lane;            // accumulator row (TMEM lane): column i0 + i_loc
+    const int cw = 32 * (warp >> 2);                     // this thread's 32 of the 64 outputs
+    const unsigned tl = tbase + ((unsigned)(32 * (warp & 3)) << 16);
+    bool ok = true;
+    int it = 0;
+    int inflight = -1;                                   // iteration whose rows are being copied
+    if (blockIdx.x < ntiles) {
+        issue(blockIdx.x);
+        inflight = 0;
     }
-    float S[MT][2][4], E[MT][2][4];
-    for (long long f = 0; f < total; ++f) {
-        const int ks = (int)(f % nks);
-        if (ks == 0) {
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const long long i0 = tile * C5_M;
+        bool w = mbar_wait_bounded(&mbar_raw, it & 1);
+        fence_after_sync();
+        // split + transpose: item = (column i, chunk of 8 rows a)
+        for (int item = tid; item < C5_M * 16; item += C5_THREADS) {
+            const int i = item & (C5_M - 1), q = item >> 7;   // lanes take consecutive columns
+            if (8 * q >= nks * 16) continue;
+            float x[8];
 #pragma unroll
-            for (int mt = 0; mt < MT; ++mt)
+            for (int e = 0; e < 8; ++e) {
+                const int a = 8 * q + e;
+                x[e] = (a < ktot && i0 + i < n) ? raw[(size_t)a * C5_M + i] : 0.f;
+            }
+            unsigned pr[3][4];
 #pragma unroll
-                for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) S[mt][nt][v] = E[mt][nt][v] = 0.f;
-        }
-        cp_wait<CB_STAGES - 2>();
-        __syncthreads();                                   // raw stage f landed; R planes free
-        {
-            const float *src = raw + (size_t)(f % CB_STAGES) * CB_RAW;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {                  // 16 row pairs x 64 columns
-                const int q = tid + u * CB_THREADS;
-                const int j = q >> 6, c = q & 63;
+            for (int h = 0; h < 4; ++h) {
                 unsigned s3[3];
-                split3(src[(2 * j) * CB_N + c], src[(2 * j + 1) * CB_N + c], s3);
-#pragma unroll
-                for (int part = 0; part < 3; ++part) rp[part * CB_PLANE + j * CB_RPP + c] = s3[part];
+                split3(x[2 * h], x[2 * h + 1], s3);
+                pr[0][h] = s3[0];
+                pr[1][h] = s3[1];
+                pr[2][h] = s3[2];
             }
+            const int kb = q >> 3;
+            const unsigned off = k128_offset(i, 8 * (q & 7));
+#pragma unroll
+            for (int pt = 0; pt < 3; ++pt)
+                *reinterpret_cast<uint4 *>(planeA + (kb * 3 + pt) * C5_APLANE + off) =
+                    make_uint4(pr[pt][0], pr[pt][1], pr[pt][2], pr[pt][3]);
         }
-        __syncthreads();                                   // R planes ready
-        if (f + CB_STAGES - 1 < total) load(f + CB_STAGES - 1);
-        cp_commit();
+        fence_async_smem();
+        fence_before_sync();
+        if (__syncthreads_or(!w)) {                      // planes ready, raw consumed
+            ok = false;
+            break;
+        }
+        inflight = -1;
+        if (tile + gridDim.x < ntiles) {
+            issue(tile + gridDim.x);
+            inflight = it + 1;
+        }
+        if (tid == 0) {
+            fence_after_sync();
+            for (int ks = 0; ks < nks; ++ks) {
+                const int kb = ks >> 2, kk = ks & 3;
+                unsigned long long ad[3], bd[3];
 #pragma unroll
-        for (int kk = 0; kk < CB_K; kk += 16) {
-            unsigned b[2][3][2];
-#pragma unroll
-            for (int part = 0; part < 3; ++part)
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt) {
-                    const unsigned *P = rp + part * CB_PLANE + (kk / 2 + t) * CB_RPP + wn + nt * 8 + g;
-                    b[nt][part][0] = P[0];
-                    b[nt][part][1] = P[4 * CB_RPP];
+                for (int pt = 0; pt < 3; ++pt) {
+                    ad[pt] = sdesc_k128(planeA + (kb * 3 + pt) * C5_APLANE) + 2 * kk;
+                    bd[pt] = sdesc_k128(planeB + (kb * 3 + pt) * C5_BPLANE) + 2 * kk;
                 }
-            const int kw = (ks * CB_K + kk) / 2 + t;
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-                unsigned a[3][4];
-#pragma unroll
-                for (int part = 0; part < 3; ++part) {
-                    const unsigned *P = cp + (size_t)part * 16 * MT * cpp + (mt * 16 + g) * cpp + kw;
-                    a[part][0] = P[0];
-                    a[part][1] = P[8 * cpp];
-                    a[part][2] = P[4];
-                    a[part][3] = P[8 * cpp + 4];
-                }
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt) {
-                    float D[4] = {0.f, 0.f, 0.f, 0.f};
-                    mma_split6(D, a, b[nt]);
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) two_sum_add(S[mt][nt][v], E[mt][nt][v], D[v]);
-                }
+                const unsigned d = tbase + ks * 64;
+                sm100::mma_bf16(d, ad[2], bd[0], idesc, false);
+                sm100::mma_bf16(d, ad[0], bd[2], idesc, true);
+                sm100::mma_bf16(d, ad[1], bd[1], idesc, true);
+                sm100::mma_bf16(d, ad[1], bd[0], idesc, true);
+                sm100::mma_bf16(d, ad[0], bd[1], idesc, true);
+                sm100::mma_bf16(d, ad[0], bd[0], idesc, true);
             }
+            mma_commit(&mbar_mma);
         }
-        if (ks == nks - 1) {
-            const long long i0 = (blockIdx.x + (f / nks) * gridDim.x) * CB_N;
+        if (!__syncthreads_and(mbar_wait_bounded(&mbar_mma, it & 1))) {
+            ok = false;
+            break;
+        }
+        fence_after_sync();
+        // add the K-step sums (each from a fresh accumulator, so the tensor
+        // core's truncation never spans more than one step) pairwise in FP32,
+        // then the epilogue of this thread's column
+        const long long i = i0 + i_loc;
+        const float dwi = (beta != 0.f && i < n) ? dw[i] : 0.f;
 #pragma unroll
-            for (int mt = 0; mt < MT; ++mt)
+        for (int h = 0; h < 2; ++h) {
+            float v[8][16];
+            const unsigned tc = tl + cw + 16 * h;
+            tmem_ld16x4(tc, tc + 64, tc + 128, tc + 192, *reinterpret_cast<float(*)[4][16]>(&v[0][0]));
+            if (nks > 4) tmem_ld16x4(tc + 256, tc + 320, tc + 384, tc + 448, *reinterpret_cast<float(*)[4][16]>(&v[4][0]));
 #pragma unroll
-                for (int nt = 0; nt < 2; ++nt)
+            for (int u = 0; u < 8; ++u)
+                if (u >= nks)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const int c = c0 + mt * 16 + g + ((v & 2) ? 8 : 0);
-                        const long long i = i0 + wn + nt * 8 + 2 * t + (v & 1);
-                        if (c < nc && i < n) {
-                            float r = S[mt][nt][v] + E[mt][nt][v];
-                            if (beta != 0.f) r = fmaf(beta * dw[i], Xc[(long long)c * ldx + i], r);
-                            out[(long long)c * ldo + i] = r;
-                        }
+                    for (int j = 0; j < 16; ++j) v[u][j] = 0.f;
+            if (i < n) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int c = cw + 16 * h + j;
+                    if (c < ncl) {
+                        float r = ((v[0][j] + v[1][j]) + (v[2][j] + v[3][j])) + ((v[4][j] + v[5][j]) + (v[6][j] + v[7][j]));
+                        if (beta != 0.f) r = fmaf(beta * dwi, Xc[(long long)(c0 + c) * ldx + i], r);
+                        out[(long long)(c0 + c) * ldo + i] = r;
                     }
+                }
+            }
         }
+        fence_before_sync();
     }
-    cp_wait<0>();
+    if (!ok) {
+        // flag it; give the copy and the MMAs still in flight a bounded wait
+        if (tid == 0 && status) atomicExch(status, 1);
+        if (inflight >= 0) mbar_wait_bounded(&mbar_raw, inflight & 1);
+        mbar_wait_bounded(&mbar_mma, it & 1);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tbase, 512);
 }
 
-template <int MT>
-int launch_combine(const float *R1, const float *R2, int k1, int ktot, long long ldr, const float *coef, int nc,
-                   long long n, float *out, long long ldo, const float *dw, const float *Xc, long long ldx,
-                   float beta, cudaStream_t s)
+// cuTensorMapEncodeTiled, from the driver through the runtime (no link
+// against the driver library); null when unavailable
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
 {
-    auto bytes_for = [](int kp) {
-        return (CB_STAGES * CB_RAW + 3 * CB_PLANE + (size_t)3 * 16 * MT * (kp / 2 + 4)) * sizeof(float);
-    };
-    const int kp = (ktot + CB_K - 1) / CB_K * CB_K;
-    const size_t smem = bytes_for(kp);
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// map of rows [0, rows) of a block (pitch ld floats) over n elements, one
+// box = 64 elements x all rows
+bool encode_rows(CUtensorMap *m, const float *base, long long n, int rows, long long ld)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = tmap_encoder();
+    if (!fn || rows < 1 || rows > 256) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)T5_K, (cuuint32_t)rows};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// tensor maps of a single-tile product (P: kp <= 128 rows from P1 / P2 split
+// at kp1; Q likewise, at most 64 rows), or maps.use = 0
+Tc05Maps tc05_maps(const float *P1, const float *P2, int kp1, int kp, const float *Q1, const float *Q2, int kq1,
+                   int kq, long long ld, long long n)
+{
+    Tc05Maps mp;
+    std::memset(&mp, 0, sizeof(mp));
+    if (kp > T5_M || kq > T5_N || n < T5_K) return mp;
+    const int h[4] = {std::min(kp1, kp), kp - std::min(kp1, kp), std::min(kq1, kq), kq - std::min(kq1, kq)};
+    const float *b[4] = {P1, P2, Q1, Q2};
+    const int off[4] = {0, h[0], T5_M, T5_M + h[2]};
+    for (int i = 0; i < 4; ++i) {
+        mp.h[i] = h[i];
+        mp.off[i] = off[i];
+        if (h[i] > 0 && (!b[i] || !encode_rows(&mp.m[i], b[i], n, h[i], ld))) {
+            std::memset(&mp, 0, sizeof(mp));
+            return mp;
+        }
+    }
+    mp.use = 1;
+    return mp;
+}
+
+// orientation of a product on the tcgen05 kernel: the operand with more
+// rows (up to 128) takes the MMA's M
+struct Tc05Shape {
+    bool swap;           // P = B, Q = A
+    int kp, kq;          // rows of P and Q
+    int gx, gy;          // tiles along Q (64 rows) and P (128 rows)
+};
+
+Tc05Shape tc05_shape(int ka, int kb)
+{
+    Tc05Shape t;
+    t.swap = kb > ka && kb <= T5_M && ka <= T5_N;
+    t.kp = t.swap ? kb : ka;
+    t.kq = t.swap ? ka : kb;
+    t.gx = (t.kq + T5_N - 1) / T5_N;
+    t.gy = (t.kp + T5_M - 1) / T5_M;
+    return t;
+}
+
+int tc05_prepare(int *nsm_out)
+{
     static bool attr[64] = {};
+    static int nsm_of[64] = {};
     int dev = 0;
     GB_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return GBFWI_EINVAL;
     if (!attr[dev]) {
-        GB_CUDA(cudaFuncSetAttribute(combine_tc_kernel<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)bytes_for(128)));
+        GB_CUDA(cudaFuncSetAttribute(atb_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T5_SMEM));
+        int nsm = 152;
+        GB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        nsm_of[dev] = nsm;
         attr[dev] = true;
     }
-    int nsm = 152, occ = 1;
-    GB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, combine_tc_kernel<MT>, CB_THREADS, smem));
-    const long long ntiles = (n + CB_N - 1) / CB_N;
-    const int ny = (nc + 63) / 64;
-    const int gx = (int)std::max<long long>(1, std::min<long long>(ntiles, (long long)nsm * std::max(occ, 1) / ny));
-    combine_tc_kernel<MT><<<dim3(gx, ny), CB_THREADS, smem, s>>>(R1, R2, k1, ktot, ldr, coef, nc, n, out, ldo, dw,
-                                                                 Xc, ldx, beta);
-    GB_LAUNCHED();
+    *nsm_out = nsm_of[dev];
     return GBFWI_OK;
 }
 
-// CTAs of atb_tc_kernel resident per SM on the current device (one wave of
-// splits fills the GPU)
-int atb_occupancy(int *nsm_out, int *occ_out)
+// K range of one split: a multiple of the 64-deep stage
+long long tc05_chunk(int ka, int kb, long long n, long long *nsplit_out)
 {
-    static int occ_of[64] = {}, nsm_of[64] = {};
-    int dev = 0;
-    GB_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return GBFWI_EINVAL;
-    if (!occ_of[dev]) {
-        GB_CUDA(cudaFuncSetAttribute(atb_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AT_SMEM));
-        int nsm = 152, occ = 1;
-        GB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, atb_tc_kernel, AT_THREADS, AT_SMEM));
-        nsm_of[dev] = nsm;
-        occ_of[dev] = std::max(occ, 1);
-    }
-    *nsm_out = nsm_of[dev];
-    *occ_out = occ_of[dev];
-    return GBFWI_OK;
+    int nsm = 152;
+    if (tc05_prepare(&nsm) != GBFWI_OK) return -1;
+    const Tc05Shape t = tc05_shape(ka, kb);
+    const long long tiles = (long long)t.gx * t.gy;
+    // one wave of CTAs (one per SM), each split at least 8 stages long
+    const long long nsplit = std::max<long long>(1, std::min<long long>(nsm / tiles, n / (8 * T5_K)));
+    const long long chunk = ((n + nsplit - 1) / nsplit + T5_K - 1) / T5_K * T5_K;
+    *nsplit_out = (n + chunk - 1) / chunk;
+    return chunk;
 }
 
 }  // namespace
 
 long long gb_tc_atb_splits(int ka, int kb, long long n)
 {
-    int nsm = 152, occ = 1;
-    if (atb_occupancy(&nsm, &occ) != GBFWI_OK) return -1;
-    const long long tiles = (long long)((kb + AT_N - 1) / AT_N) * ((ka + AT_M - 1) / AT_M);
-    // one wave of CTAs, each split at least 8 K steps long
-    long long nsplit = std::max<long long>(1, std::min<long long>((long long)nsm * occ / tiles, n / (8 * AT_K)));
-    const long long chunk = ((n + nsplit - 1) / nsplit + AT_K - 1) / AT_K * AT_K;
-    return (n + chunk - 1) / chunk;
+    long long nsplit = 0;
+    if (tc05_chunk(ka, kb, n, &nsplit) < 1) return -1;
+    return nsplit;
 }
 
 int gb_tc_atb(const float *A1, const float *A2, int ka1, int ka, const float *B1, const float *B2, int kb1, int kb,
               long long ld, long long n, double *part, size_t part_doubles, double *out, long long ldo,
-              cudaStream_t s)
+              int *status, cudaStream_t s)
 {
     if (ka < 1 || kb < 1 || n < 1) return GBFWI_OK;
-    if (ld % 4 != 0 || ((uintptr_t)A1 & 15) || ((uintptr_t)A2 & 15) || ((uintptr_t)B1 & 15) || ((uintptr_t)B2 & 15))
+    if (ld % T5_K != 0 || ld < n || ((uintptr_t)A1 & 255) || ((uintptr_t)A2 & 255) || ((uintptr_t)B1 & 255) ||
+        ((uintptr_t)B2 & 255))
         return GBFWI_EINVAL;
-    const long long nsplit0 = gb_tc_atb_splits(ka, kb, n);
-    if (nsplit0 < 1) return GBFWI_ECUDA;
-    const long long chunk = ((n + nsplit0 - 1) / nsplit0 + AT_K - 1) / AT_K * AT_K;
-    const long long nsplit = (n + chunk - 1) / chunk;
+    long long nsplit = 0;
+    const long long chunk = tc05_chunk(ka, kb, n, &nsplit);
+    if (chunk < 1) return GBFWI_ECUDA;
     if ((size_t)nsplit * ka * kb > part_doubles) return GBFWI_EINVAL;
-    const int gx = (kb + AT_N - 1) / AT_N, gy = (ka + AT_M - 1) / AT_M;
-    atb_tc_kernel<<<dim3(gx, gy, (unsigned)nsplit), AT_THREADS, AT_SMEM, s>>>(A1, A2, ka1, ka, B1, B2, kb1, kb, ld, n,
-                                                                            chunk, part);
+    const Tc05Shape t = tc05_shape(ka, kb);
+    // part[sx][a][b]: (P, Q) = (A, B) writes row p at a, or (B, A) at b
+    const long long sp = t.swap ? 1 : kb, sq = t.swap ? kb : 1;
+    if (t.swap) {
+        const Tc05Maps mp = tc05_maps(B1, B2, kb1, kb, A1, A2, ka1, ka, ld, n);
+        atb_tc05_kernel<<<dim3(t.gx, t.gy, (unsigned)nsplit), T5_THREADS, T5_SMEM, s>>>(
+            mp, B1, B2, kb1, kb, A1, A2, ka1, ka, ld, n, chunk, part, (long long)ka * kb, sp, sq, status);
+    } else {
+        const Tc05Maps mp = tc05_maps(A1, A2, ka1, ka, B1, B2, kb1, kb, ld, n);
+        atb_tc05_kernel<<<dim3(t.gx, t.gy, (unsigned)nsplit), T5_THREADS, T5_SMEM, s>>>(
+            mp, A1, A2, ka1, ka, B1, B2, kb1, kb, ld, n, chunk, part, (long long)ka * kb, sp, sq, status);
+    }
     GB_LAUNCHED();
     const int nab = ka * kb;
     split_reduce_kernel<<<(nab + 255) / 256, 256, 0, s>>>(part, (int)nsplit, ka, kb, out, ldo);
@@ -498,13 +682,47 @@ int gb_tc_atb(const float *A1, const float *A2, int ka1, int ka, const float *B1
 
 int gb_tc_combine(const float *R1, const float *R2, int k1, int ktot, long long ldr, const float *coef, int nc,
                   long long n, float *out, long long ldo, const float *dw, const float *Xc, long long ldx,
-                  float beta, cudaStream_t s)
+                  float beta, int *status, cudaStream_t s)
 {
     if (nc < 1 || n < 1) return GBFWI_OK;
-    if (ktot < 1 || ktot > 128 || ldr % 4 != 0 || ((uintptr_t)R1 & 15) || ((uintptr_t)R2 & 15))
+    if (ktot < 1 || ktot > 128 || ldr % C5_KB != 0 || ldr < n || ((uintptr_t)R1 & 255) || ((uintptr_t)R2 & 255))
         return GBFWI_EINVAL;
-    const int m = std::min(nc, 64);
-    if (m <= 16) return launch_combine<1>(R1, R2, k1, ktot, ldr, coef, nc, n, out, ldo, dw, Xc, ldx, beta, s);
-    if (m <= 32) return launch_combine<2>(R1, R2, k1, ktot, ldr, coef, nc, n, out, ldo, dw, Xc, ldx, beta, s);
-    return launch_combine<4>(R1, R2, k1, ktot, ldr, coef, nc, n, out, ldo, dw, Xc, ldx, beta, s);
+    static bool attr[64] = {};
+    static int nsm_of[64] = {};
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return GBFWI_EINVAL;
+    if (!attr[dev]) {
+        GB_CUDA(cudaFuncSetAttribute(combine_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C5_SMEM));
+        int nsm = 152;
+        GB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        nsm_of[dev] = nsm;
+        attr[dev] = true;
+    }
+    // tensor maps of the two row blocks: box 128 columns x all rows of the block
+    Cb5Maps mp;
+    std::memset(&mp, 0, sizeof(mp));
+    mp.h[0] = std::min(k1, ktot);
+    mp.h[1] = ktot - mp.h[0];
+    mp.use = n >= C5_M;
+    const float *blk[2] = {R1, R2};
+    PFN_cuTensorMapEncodeTiled_v12000 fn = tmap_encoder();
+    for (int b = 0; b < 2 && mp.use; ++b) {
+        if (mp.h[b] == 0) continue;
+        const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)mp.h[b]};
+        const cuuint64_t strides[1] = {(cuuint64_t)ldr * sizeof(float)};
+        const cuuint32_t box[2] = {(cuuint32_t)C5_M, (cuuint32_t)mp.h[b]};
+        const cuuint32_t es[2] = {1, 1};
+        mp.use = fn && blk[b] &&
+                 fn(&mp.m[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(blk[b]), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    const long long ntiles = (n + C5_M - 1) / C5_M;
+    const int ny = (nc + C5_N - 1) / C5_N;
+    const int gx = (int)std::max<long long>(1, std::min<long long>(ntiles, std::max(1, nsm_of[dev] / ny)));
+    combine_tc05_kernel<<<dim3(gx, ny), C5_THREADS, C5_SMEM, s>>>(mp, R1, R2, k1, ktot, ldr, coef, nc, n, out, ldo, dw,
+                                                                 Xc, ldx, beta, status);
+    GB_LAUNCHED();
+    return GBFWI_OK;
 }
