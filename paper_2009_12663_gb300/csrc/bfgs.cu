@@ -335,8 +335,8 @@ __global__ void __launch_bounds__(512) chol_kernel(const double *__restrict__ G,
 // overwritten by its eigenvalues on the diagonal); U accumulates the
 // eigenvectors as columns (must hold I on entry).  Round-robin pairing gives
 // P/2 disjoint rotations per round (P = p rounded up to even); the pairing
-// of every round is tabulated once, and each thread keeps the same
-// (pair, column) items in every round.  A pair is rotated only while
+// of every round is tabulated once; a round rotates every 2 x 2 block of A
+// (a pair of rows by a pair of columns) on both sides in one pass.  A pair is rotated only while
 // |a_pq| > rel_eps sqrt(|a_pp a_qq|) (the relative threshold of Demmel &
 // Veselic 1992, which also resolves small eigenvalues of a graded matrix)
 // and |a_pq| > abs_eps |A|_F (below that an entry is rounding noise of the
@@ -371,9 +371,7 @@ __device__ void block_jacobi(T *A, T *U, int p, T *cs, short *pairs, int max_swe
     }
     __syncthreads();
     const T abs_tol = abs_eps * sqrt(fro);
-    const int items = npair * p;                // (pair, column) items of one update
-    // this thread's items q = t + i nt, as (pair m, column l), stepped without division
-    const int m0 = t / p, l0 = t - (t / p) * p, dm = nt / p, dl = nt - (nt / p) * p;
+    const int nblk = npair * npair;             // 2 x 2 blocks (pair of rows, pair of columns) of A
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (t == 0) rotated = 0;
         __syncthreads();
@@ -397,26 +395,34 @@ __device__ void block_jacobi(T *A, T *U, int p, T *cs, short *pairs, int max_swe
                 cs[2 * m + 1] = sn;
             }
             __syncthreads();
-            for (int q = t, m = m0, l = l0; q < items; q += nt, m += dm, l += dl) {   // rows: A <- J^T A
-                if (l >= p) { l -= p; ++m; }
-                const T sn = cs[2 * m + 1];
-                if (sn == 0) continue;
-                const int pp = pr[2 * m], qq = pr[2 * m + 1];
-                const T c = cs[2 * m];
-                const T x = A[pp * p + l], y = A[qq * p + l];
-                A[pp * p + l] = c * x - sn * y;
-                A[qq * p + l] = sn * x + c * y;
+            // A <- J^T A J in one pass: every 2 x 2 block (rows of pair m1,
+            // columns of pair m2) is read once, rotated on both sides, written
+            // once; U <- U J on the same pass
+            for (int q = t; q < nblk; q += nt) {
+                const int m1 = q / npair, m2 = q - m1 * npair;
+                const T s1 = cs[2 * m1 + 1], s2 = cs[2 * m2 + 1];
+                if (s1 == 0 && s2 == 0) continue;
+                const T c1 = cs[2 * m1], c2 = cs[2 * m2];
+                const int p1 = pr[2 * m1], q1 = pr[2 * m1 + 1], p2 = pr[2 * m2], q2 = pr[2 * m2 + 1];
+                const bool hq1 = q1 < p, hq2 = q2 < p;
+                const T a = A[p1 * p + p2];
+                const T b = hq2 ? A[p1 * p + q2] : (T)0;
+                const T cc = hq1 ? A[q1 * p + p2] : (T)0;
+                const T d = (hq1 && hq2) ? A[q1 * p + q2] : (T)0;
+                // rows (pair m1), then columns (pair m2)
+                const T ra = c1 * a - s1 * cc, rc = s1 * a + c1 * cc;
+                const T rb = c1 * b - s1 * d, rd = s1 * b + c1 * d;
+                A[p1 * p + p2] = c2 * ra - s2 * rb;
+                if (hq2) A[p1 * p + q2] = s2 * ra + c2 * rb;
+                if (hq1) A[q1 * p + p2] = c2 * rc - s2 * rd;
+                if (hq1 && hq2) A[q1 * p + q2] = s2 * rc + c2 * rd;
             }
-            __syncthreads();
-            for (int q = t, m = m0, l = l0; q < items; q += nt, m += dm, l += dl) {   // columns: A <- A J, U <- U J
-                if (l >= p) { l -= p; ++m; }
+            for (int q = t; q < p * npair; q += nt) {
+                const int l = q / npair, m = q - l * npair;
                 const T sn = cs[2 * m + 1];
                 if (sn == 0) continue;
                 const int pp = pr[2 * m], qq = pr[2 * m + 1];
                 const T c = cs[2 * m];
-                const T x = A[l * p + pp], y = A[l * p + qq];
-                A[l * p + pp] = c * x - sn * y;
-                A[l * p + qq] = sn * x + c * y;
                 const T u = U[l * p + pp], v = U[l * p + qq];
                 U[l * p + pp] = c * u - sn * v;
                 U[l * p + qq] = sn * u + c * v;
@@ -577,56 +583,68 @@ __device__ void select_eigenpairs(const float *Af, const float *Uf, int r, int r
     for (int k = r + t; k < rank; k += nt) lam[k] = 0.0;
 }
 
-// Single-pass randomized SVD core (Algorithm 3) with r <= p basis vectors:
-// Omega (Q^T X) = Q^T E, solved directly when r = p (Omega = QE QX^-1) and
-// in the least-squares sense Omega = QE QX^T (QX QX^T)^-1 when r < p
-// (Gauss-Jordan with partial pivoting in FP64), symmetrised, then
-// eigendecomposed; eigenpairs by |lambda| descending.  QE, QX: [r][p] FP64
-// with row stride ldq.
-// Outputs lam[rank] (zeros beyond r) and coef[rank][r] = U^T (zero rows
-// beyond r).  work: >= 4 r^2 + 4 r doubles (or shared memory).
-__global__ void omega_ls_kernel(const double *__restrict__ QE, const double *__restrict__ QX, long long ldq, int r,
-                                int p, int rank, double *work, double *__restrict__ lam, float *__restrict__ coef,
-                                int *__restrict__ flag, int use_smem)
+
+// d_i = 1 / sqrt(G_ii) (0 for an empty row), G <- D G D: the pivoted
+// Cholesky then compares directions, not the scales of S and B0 Y
+// Omega from Omega (Q^T X) = Q^T E (Algorithm 3) in four steps, the FP64
+// work spread over SMs where it is independent:
+//   omega_system_kernel (block i): row i of the system N Omega^T = Bm^T:
+//     square Q^T X: N = (Q^T X)^T, Bm^T = (Q^T E)^T; wide Q^T X (r < p): the
+//     normal equations N = QX QX^T, Bm = QE QX^T;
+//   lu_kernel (one CTA): N = P^T L U by partial pivoting (first row among
+//     equal magnitudes), one barrier per elimination step; a zero pivot sets
+//     flag 3 and is taken as 1;
+//   lu_solve_kernel (block c): column c of Omega^T from its right-hand side;
+//   then sym_kernel and eig_select_kernel.
+__global__ void __launch_bounds__(32) omega_system_kernel(const double *__restrict__ QE,
+                                                          const double *__restrict__ QX, long long ldq, int r, int p,
+                                                          double *__restrict__ N, double *__restrict__ Bt)
 {
-    extern __shared__ double smem_work[];
-    if (use_smem) work = smem_work;
-    const int t = threadIdx.x, nt = blockDim.x;
-    double *Aug = work;                     // [r][2r]: [N | Bm^T], N = QX QX^T, Bm = QE QX^T
-    double *A = Aug + 2LL * r * r;          // [r][r]
-    double *U = A + (long long)r * r;       // [r][r]
-    double *cs = U + (long long)r * r;      // >= r + 1
-    __shared__ int piv_row;
-    if (r == p) {
-        // square Q^T X: solve (Q^T X)^T Omega^T = (Q^T E)^T directly
-        for (int q = t; q < r * r; q += nt) {
-            const int i = q / r, j = q % r;
-            Aug[(long long)i * 2 * r + j] = QX[(long long)j * ldq + i];
-            Aug[(long long)i * 2 * r + r + j] = QE[(long long)j * ldq + i];
-        }
-    } else {
-        // least squares through the normal equations of the wide Q^T X
-        for (int q = t; q < r * r; q += nt) {
-            const int i = q / r, j = q % r;
-            double nij = 0.0, bji = 0.0;
-            for (int c = 0; c < p; ++c) {
-                nij += QX[(long long)i * ldq + c] * QX[(long long)j * ldq + c];
-                bji += QE[(long long)j * ldq + c] * QX[(long long)i * ldq + c];   // Bm[j][i]
+    const int i = blockIdx.x, lane = threadIdx.x;
+    if (i >= r) return;
+    for (int j = 0; j < r; ++j) {
+        if (r == p) {
+            if (lane == 0) {
+                N[(long long)i * r + j] = QX[(long long)j * ldq + i];
+                Bt[(long long)i * r + j] = QE[(long long)j * ldq + i];
             }
-            Aug[(long long)i * 2 * r + j] = nij;
-            Aug[(long long)i * 2 * r + r + j] = bji;                          // Bm^T[i][j]
+            continue;
+        }
+        double nij = 0.0, bji = 0.0;
+        for (int c = lane; c < p; c += 32) {
+            const double xi = QX[(long long)i * ldq + c];
+            nij += xi * QX[(long long)j * ldq + c];
+            bji += QE[(long long)j * ldq + c] * xi;
+        }
+        nij = warp_sum(nij);
+        bji = warp_sum(bji);
+        if (lane == 0) {
+            N[(long long)i * r + j] = nij;
+            Bt[(long long)i * r + j] = bji;               // Bm^T[i][j] = Bm[j][i]
         }
     }
+}
+
+__global__ void __launch_bounds__(512) lu_kernel(double *__restrict__ M, double *__restrict__ L, int *__restrict__ perm,
+                                                 int r, int *__restrict__ flag, int use_smem)
+{
+    extern __shared__ double lu_smem[];
+    double *A = use_smem ? lu_smem : M;
+    double *Ls = use_smem ? lu_smem + (size_t)r * r : L;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int a = ty; a < r; a += 16)
+        for (int c = tx; c < r; c += 32) {
+            if (use_smem) A[a * r + c] = M[(long long)a * r + c];
+            Ls[a * r + c] = 0.0;
+        }
     __syncthreads();
-    // Gauss-Jordan with partial pivoting: N Omega^T = Bm^T
     for (int j = 0; j < r; ++j) {
-        if (t < 32) {
-            // partial pivot (first row among equals), warp 0
+        if (threadIdx.x < 32) {
             int best = -1;
             double bv = -1.0;
-            for (int rr = j + t; rr < r; rr += 32) {
-                const double v = fabs(Aug[(long long)rr * 2 * r + j]);
-                if (v > bv) { bv = v; best = rr; }
+            for (int a = j + tx; a < r; a += 32) {
+                const double v = fabs(A[a * r + j]);
+                if (v > bv) { bv = v; best = a; }
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
@@ -634,54 +652,97 @@ __global__ void omega_ls_kernel(const double *__restrict__ QE, const double *__r
                 const int ob = __shfl_down_sync(0xffffffffu, best, off);
                 if (ov > bv || (ov == bv && ob >= 0 && (best < 0 || ob < best))) { bv = ov; best = ob; }
             }
-            if (t == 0) {
+            best = __shfl_sync(0xffffffffu, best, 0);
+            bv = __shfl_sync(0xffffffffu, bv, 0);
+            if (best < 0) best = j;
+            if (tx == 0) {
                 if (!(bv > 0.0)) *flag = 3;
-                piv_row = best < 0 ? j : best;
+                perm[j] = best;
             }
+            if (best != j)
+                for (int c = tx; c < r; c += 32) {
+                    const double x = A[j * r + c];
+                    A[j * r + c] = A[best * r + c];
+                    A[best * r + c] = x;
+                    if (c < j) {
+                        const double y = Ls[j * r + c];
+                        Ls[j * r + c] = Ls[best * r + c];
+                        Ls[best * r + c] = y;
+                    }
+                }
         }
         __syncthreads();
-        int pr = piv_row;
-        if (pr != j)
-            for (int c = t; c < 2 * r; c += nt) {
-                double a = Aug[(long long)j * 2 * r + c];
-                Aug[(long long)j * 2 * r + c] = Aug[(long long)pr * 2 * r + c];
-                Aug[(long long)pr * 2 * r + c] = a;
-            }
-        __syncthreads();
-        double d = Aug[(long long)j * 2 * r + j];
+        double d = A[j * r + j];
         if (d == 0.0) d = 1.0;
-        const double dinv = 1.0 / d;
-        __syncthreads();
-        for (int c = t; c < 2 * r; c += nt) Aug[(long long)j * 2 * r + c] *= dinv;
-        __syncthreads();
-        for (int q = t; q < r * 2 * r; q += nt) {
-            int rr = q / (2 * r), c = q % (2 * r);
-            if (rr == j || c == j) continue;
-            Aug[(long long)rr * 2 * r + c] -= Aug[(long long)rr * 2 * r + j] * Aug[(long long)j * 2 * r + c];
+        const double inv = 1.0 / d;
+        for (int a = j + 1 + ty; a < r; a += 16) {
+            const double l = A[a * r + j] * inv;
+            for (int c = j + 1 + tx; c < r; c += 32) A[a * r + c] -= l * A[j * r + c];
+            if (tx == 0) Ls[a * r + j] = l;
         }
         __syncthreads();
-        for (int rr = t; rr < r; rr += nt)
-            if (rr != j) Aug[(long long)rr * 2 * r + j] = 0.0;
-        __syncthreads();
     }
-    // Omega symmetrised, eigendecomposed in FP32 (absolute eigenvalue error
-    // ~1e-7 |Omega|; FP64 sweeps cost ~60x more on this part)
-    float *Af = reinterpret_cast<float *>(U);             // r^2 floats
-    float *Uf = Af + (long long)r * r;                     // r^2 floats (U holds 2 r^2)
-    float *csf = reinterpret_cast<float *>(cs);
-    for (int q = t; q < r * r; q += nt) {
-        int i = q / r, j = q % r;
-        double oij = Aug[(long long)j * 2 * r + r + i];   // Omega[i][j] = Omega^T[j][i]
-        double oji = Aug[(long long)i * 2 * r + r + j];
-        Af[q] = (float)(0.5 * (oij + oji));
-        Uf[q] = (i == j) ? 1.f : 0.f;
-    }
-    block_jacobi<float>(Af, Uf, r, csf, reinterpret_cast<short *>(A), 40);
-    select_eigenpairs(Af, Uf, r, rank, lam, coef, flag);
+    if (use_smem)
+        for (int a = ty; a < r; a += 16)
+            for (int c = tx; c < r; c += 32) {
+                M[(long long)a * r + c] = A[a * r + c];
+                L[(long long)a * r + c] = Ls[a * r + c];
+            }
 }
 
-// d_i = 1 / sqrt(G_ii) (0 for an empty row), G <- D G D: the pivoted
-// Cholesky then compares directions, not the scales of S and B0 Y
+// (L and U staged in shared memory first when they fit: the solves are
+// chains of dependent steps, each of which would otherwise wait on L2)
+__global__ void __launch_bounds__(32) lu_solve_kernel(const double *__restrict__ U, const double *__restrict__ L,
+                                                      const int *__restrict__ perm, const double *__restrict__ Bt,
+                                                      int r, double *__restrict__ X, int use_smem)
+{
+    __shared__ double x[256];
+    extern __shared__ double lus_smem[];
+    const int c = blockIdx.x, lane = threadIdx.x;
+    if (c >= r) return;
+    if (use_smem) {
+        double *Us = lus_smem, *Lsm = lus_smem + (size_t)r * r;
+        for (int q = lane; q < r * r; q += 32) {
+            Us[q] = U[q];
+            Lsm[q] = L[q];
+        }
+        __syncwarp();
+        U = Us;
+        L = Lsm;
+    }
+    for (int i = lane; i < r; i += 32) x[i] = Bt[(long long)i * r + c];
+    __syncwarp();
+    if (lane == 0)
+        for (int j = 0; j < r; ++j) {
+            const int pj = perm[j];
+            if (pj != j) {
+                const double v = x[j];
+                x[j] = x[pj];
+                x[pj] = v;
+            }
+        }
+    __syncwarp();
+    for (int i = 1; i < r; ++i) {                        // L y = P b (unit lower)
+        double sacc = 0.0;
+        for (int j = lane; j < i; j += 32) sacc += L[(long long)i * r + j] * x[j];
+        sacc = warp_sum(sacc);
+        if (lane == 0) x[i] -= sacc;
+        __syncwarp();
+    }
+    for (int i = r - 1; i >= 0; --i) {                   // U x = y
+        double sacc = 0.0;
+        for (int j = i + 1 + lane; j < r; j += 32) sacc += U[(long long)i * r + j] * x[j];
+        sacc = warp_sum(sacc);
+        if (lane == 0) {
+            double d = U[(long long)i * r + i];
+            if (d == 0.0) d = 1.0;
+            x[i] = (x[i] - sacc) / d;
+        }
+        __syncwarp();
+    }
+    for (int i = lane; i < r; i += 32) X[(long long)i * r + c] = x[i];
+}
+
 __global__ void gram_scale_kernel(double *__restrict__ G, int m, double *__restrict__ d)
 {
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -796,10 +857,22 @@ __global__ void philox_normal_kernel(float *__restrict__ X, long long total, lon
                                      unsigned long long seed)
 {
     const float two_pi = 6.28318530717958647692f;
+    const bool small = total + 4 < (1LL << 32);
     for (long long blk = blockIdx.x * (long long)blockDim.x + threadIdx.x; blk * 4 < total;
          blk += (long long)gridDim.x * blockDim.x) {
         unsigned c[4] = {(unsigned)(blk & 0xFFFFFFFFull), (unsigned)(blk >> 32), 0u, 0u};
         philox10(c, (unsigned)(seed & 0xFFFFFFFFull), (unsigned)(seed >> 32));
+        // row and column of the first of the four elements, one division per
+        // counter (32-bit when the block fits), then stepped along the row
+        long long row, col;
+        if (small) {
+            const unsigned e0 = (unsigned)(blk * 4), nn = (unsigned)n;
+            row = e0 / nn;
+            col = e0 - (unsigned)row * nn;
+        } else {
+            row = (blk * 4) / n;
+            col = blk * 4 - row * n;
+        }
 #pragma unroll
         for (int pr = 0; pr < 2; ++pr) {
             float u1 = ((float)(c[2 * pr] >> 8) + 1.0f) * (1.0f / 16777216.0f);
@@ -808,8 +881,10 @@ __global__ void philox_normal_kernel(float *__restrict__ X, long long total, lon
             float sn, cn;
             sincosf(two_pi * u2, &sn, &cn);
             long long e = blk * 4 + 2 * pr;
-            if (e < total) X[(e / n) * ld + e % n] = rad * cn;
-            if (e + 1 < total) X[((e + 1) / n) * ld + (e + 1) % n] = rad * sn;
+            if (e < total) X[row * ld + col] = rad * cn;
+            if (++col == n) { col = 0; ++row; }
+            if (e + 1 < total) X[row * ld + col] = rad * sn;
+            if (++col == n) { col = 0; ++row; }
         }
     }
 }
@@ -1150,7 +1225,6 @@ int lowrank_randomized(gbfwi_bfgs *h, const float *X, int p, int rank, unsigned 
     const int use_smem = ws <= 200 * 1024;
     if (use_smem) {
         GB_CUDA(cudaFuncSetAttribute(gram_pivchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
-        GB_CUDA(cudaFuncSetAttribute(omega_ls_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
     }
     GB_TRY(atb(h, E, nullptr, p, p, E, nullptr, p, p, G, p, s));
     gram_pivchol_kernel<<<1, 512, use_smem ? ws : 0, s>>>(G, p, 1e-4, work, coef, rdev, flag, use_smem);
@@ -1183,8 +1257,25 @@ int lowrank_randomized(gbfwi_bfgs *h, const float *X, int p, int rank, unsigned 
         // 3. [Q^T E, Q^T X] in one pass over Q (Omega = (Q^T E)(Q^T X)^-1
         //    amplifies their error by cond(Q^T X)); Omega by least squares; eigenpairs
         GB_TRY(atb(h, Qf, nullptr, r, r, E, Xd, p, 2 * p, QEX, 2 * p, s));
-        omega_ls_kernel<<<1, 512, use_smem ? ws : 0, s>>>(QEX, QEX + p, 2 * p, r, p, rank, work, lam, coef, flag,
-                                                          use_smem);
+        // N (in A), Bm^T (in G), N = P^T L U (U in A, L in R2), Omega^T (in Rinv)
+        int *perm = reinterpret_cast<int *>(work + pp);
+        omega_system_kernel<<<r, 32, 0, s>>>(QEX, QEX + p, 2 * p, r, p, A, G);
+        GB_LAUNCHED();
+        const size_t wl = (size_t)2 * r * r * sizeof(double);
+        const int lu_smem = wl <= 200 * 1024;
+        if (lu_smem) GB_CUDA(cudaFuncSetAttribute(lu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wl));
+        lu_kernel<<<1, 512, lu_smem ? wl : 0, s>>>(A, R2, perm, r, flag, lu_smem);
+        GB_LAUNCHED();
+        if (lu_smem) GB_CUDA(cudaFuncSetAttribute(lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wl));
+        lu_solve_kernel<<<r, 32, lu_smem ? wl : 0, s>>>(A, R2, perm, G, r, Rinv, lu_smem);
+        GB_LAUNCHED();
+        sym_kernel<<<1, 512, 0, s>>>(Rinv, r);
+        GB_LAUNCHED();
+        const size_t we = ((size_t)r * r + r + 16 + ((size_t)r + 2) * (r + 2) / 4) * sizeof(double);
+        const int use_smem2 = we <= 200 * 1024;
+        if (use_smem2)
+            GB_CUDA(cudaFuncSetAttribute(eig_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)we));
+        eig_select_kernel<<<1, 512, use_smem2 ? we : 0, s>>>(Rinv, r, rank, work, lam, coef, flag, use_smem2);
         GB_LAUNCHED();
     } else {
         // 3. second pass: E2 = (B - B0) Q (into E, free now), C = Q E2^T
