@@ -39,7 +39,9 @@ struct gbfwi_bfgs {
     DevBuf S, Y, BY, B0;       // [kmax][n] x 3, [n]
     std::vector<double> SY;    // [kmax][kmax]: SY[i*kmax + j] = s_i^T y_j (i <= j)
     std::vector<double> YBY;   // [kmax][kmax]: y_i^T B0 y_j
+    std::vector<double> SS, SB, BB;   // [kmax][kmax]: s_i^T s_j, s_i^T B0 y_j, (B0 y_i)^T (B0 y_j)
     DevBuf dSY, dYBY;          // device copies
+    DevBuf dG;                 // [2k][2k] FP64: W^T W with W = [S, B0 Y] (rows s_i, then B0 y_i)
     DevBuf part;               // split-K partials
     DevBuf small;              // FP64 small matrices
     DevBuf coef;               // FP32 combination coefficients
@@ -47,7 +49,7 @@ struct gbfwi_bfgs {
     DevBuf stage;              // host staging
     DevBuf flag;
     DevBuf status;             // int: nonzero after a product kernel's bounded wait gave up
-    DevBuf ex;                 // FP64 scratch of the exact low-rank decomposition
+    DevBuf ex;                 // FP64 scratch of the low-rank decompositions
 };
 
 namespace {
@@ -119,6 +121,41 @@ __global__ void atb_reduce(const double *__restrict__ part, int nsplit, int nab,
     for (int sx = 0; sx < nsplit; ++sx) s += part[(long long)sx * nab + q];
     int a = q / kb, b = q - a * kb;
     out[(long long)a * ldo + b] = s;
+}
+
+// Dot products of a new pair with the store (the update of the Gram
+// matrices): CTA (split, a) takes row a of [S_0..S_{k1-1}, B0Y_0..B0Y_{k1-1}]
+// against the three vectors (y, s, B0 y) with compensated (Dot2) sums, then
+// an FP64 tree over its threads; part[sx][a][b] is reduced over the splits
+// by atb_reduce.
+__global__ void __launch_bounds__(256) pair_dots_kernel(const float *__restrict__ S, const float *__restrict__ BY,
+                                                        long long ld, int k1, const float *__restrict__ y,
+                                                        const float *__restrict__ sv, const float *__restrict__ by,
+                                                        long long n, long long chunk, double *__restrict__ part)
+{
+    __shared__ double red[3][256];
+    const int sx = blockIdx.x, a = blockIdx.y, t = threadIdx.x;
+    const long long ib = (long long)sx * chunk, ie = min(n, ib + chunk);
+    const float *ar = a < k1 ? S + (long long)a * ld : BY + (long long)(a - k1) * ld;
+    float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
+    for (long long i = ib + t; i < ie; i += blockDim.x) {
+        const float av = __ldg(ar + i);
+        dot2_term(av, __ldg(y + i), hi[0], lo[0]);
+        dot2_term(av, __ldg(sv + i), hi[1], lo[1]);
+        dot2_term(av, __ldg(by + i), hi[2], lo[2]);
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) red[b][t] = (double)hi[b] + (double)lo[b];
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (t < h)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) red[b][t] += red[b][t + h];
+        __syncthreads();
+    }
+    if (t == 0)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) part[((long long)sx * 2 * k1 + a) * 3 + b] = red[b][0];
 }
 
 // out[c][i] = sum_a coef[c][a] row_a[i] + beta * dw[i] * Xc[c][i]  for c in [c0, c0 + cn)
@@ -204,27 +241,34 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Compact-form middle product for each column c of T ([2k][p]: rows 0..k-1
-// S^T x_c, rows k..2k-1 (B0 Y)^T x_c):
+// Compact-form middle product for each column c of T ([2k][p], row stride
+// p: rows 0..k-1 S^T x_c, rows k..2k-1 (B0 Y)^T x_c):
 //   cv = R^-1 a, top = R^-T ((D + gamma Y^T B0 Y) cv - gamma t2)
 //   coef[c] = [top, -gamma cv]
-// one warp per probe column c (block c): the k-long FP64 triangular solves
-// and the Y^T B0 Y product, dot products split over the lanes; FP64 is
-// spread over p SMs instead of one
+// i.e. coef[c] = M T_c with M the middle matrix of the compact form.  One
+// warp per probe column c (block c): the k-long FP64 triangular solves and
+// the Y^T B0 Y product, dot products split over the lanes; FP64 is spread
+// over p SMs instead of one.  The reciprocals of the diagonal of R are
+// formed once, in parallel (dynamic shared memory: k doubles), so the
+// solves' dependent chains hold no division.  Outputs (either may be null):
+// coef FP32 and coefd FP64, both [p][2k].
 __global__ void __launch_bounds__(32) middle_kernel(const double *__restrict__ T, const double *__restrict__ SY,
                                                     const double *__restrict__ YBY, int k, int kmax, int p,
                                                     double gamma, double *__restrict__ scratch,
-                                                    float *__restrict__ coef)
+                                                    float *__restrict__ coef, double *__restrict__ coefd)
 {
+    extern __shared__ double rdiag[];
     const int c = blockIdx.x, lane = threadIdx.x;
     if (c >= p) return;
+    for (int i = lane; i < k; i += 32) rdiag[i] = 1.0 / __ldg(SY + (long long)i * kmax + i);
+    __syncwarp();
     double *cv = scratch + (long long)c * 2 * k, *d = cv + k;
     // R cv = T_top (back substitution), R_ij = s_i^T y_j upper
     for (int i = k - 1; i >= 0; --i) {
         double s = 0.0;
         for (int j = i + 1 + lane; j < k; j += 32) s += __ldg(SY + (long long)i * kmax + j) * cv[j];
         s = warp_sum(s);
-        if (lane == 0) cv[i] = (__ldg(T + (long long)i * p + c) - s) / __ldg(SY + (long long)i * kmax + i);
+        if (lane == 0) cv[i] = (__ldg(T + (long long)i * p + c) - s) * rdiag[i];
         __syncwarp();
     }
     for (int i = 0; i < k; ++i) {
@@ -240,95 +284,42 @@ __global__ void __launch_bounds__(32) middle_kernel(const double *__restrict__ T
         double s = 0.0;
         for (int j = lane; j < i; j += 32) s += __ldg(SY + (long long)j * kmax + i) * d[j];
         s = warp_sum(s);
-        if (lane == 0) d[i] = (d[i] - s) / __ldg(SY + (long long)i * kmax + i);
+        if (lane == 0) d[i] = (d[i] - s) * rdiag[i];
         __syncwarp();
     }
     for (int i = lane; i < k; i += 32) {
-        coef[(long long)c * 2 * k + i] = (float)d[i];
-        coef[(long long)c * 2 * k + k + i] = (float)(-gamma * cv[i]);
+        const double top = d[i], bot = -gamma * cv[i];
+        if (coef) {
+            coef[(long long)c * 2 * k + i] = (float)top;
+            coef[(long long)c * 2 * k + k + i] = (float)bot;
+        }
+        if (coefd) {
+            coefd[(long long)c * 2 * k + i] = top;
+            coefd[(long long)c * 2 * k + k + i] = bot;
+        }
     }
 }
 
-// Cholesky G + shift tr(G) I = R^T R (R upper, p x p), then coef = R^-T
-// (lower) for the row combination Q = R^-T E (one CholeskyQR pass; the
-// first pass of shifted CholeskyQR3 passes shift > 0).  FP32 arithmetic
-// (GB300 runs FP64 at 1/64 of the FP32 rate): a pass only needs an
-// invertible triangular R that makes the rows nearly orthonormal, since
-// R^-T E spans the rows of E for any invertible R, and the next pass
-// removes what is left; the shift (1e-5 of the trace) keeps the FP32 Gram
-// matrix definite.  The Gram matrix, the factor and its inverse live in
-// shared memory when 3 p^2 floats fit (use_smem), else in the global scratch
-// A, Rinv and the coefficient array.
-__global__ void __launch_bounds__(512) chol_kernel(const double *__restrict__ G, int p, double shift, float *A,
-                                                   float *Rinv, float *__restrict__ coef, int *__restrict__ flag,
-                                                   int use_smem)
+// out[i][j] = sum_l A(i, l) B(l, j), i < M, j < N, l < K, with A(i, l) =
+// A[i ar + l ac] and B(l, j) = B[l br + j bc] (any transposition by the
+// strides), FP64 accumulation in l order; one thread per output element,
+// blocks (N / 32, M): the small FP64 products of the decompositions spread
+// over the SMs (GB300 runs about two FP64 FMAs per clock per SM).  Outputs
+// (either may be null): out FP64 and outf FP32, both with row stride ldo.
+template <typename TA>
+__global__ void __launch_bounds__(32) small_gemm_kernel(int M, int N, int K, const TA *__restrict__ A, long long ar,
+                                                        long long ac, const double *__restrict__ B, long long br,
+                                                        long long bc, double *__restrict__ out,
+                                                        float *__restrict__ outf, long long ldo)
 {
-    // A: the Gram matrix, then the right-hand sides B of R X = I; R: the
-    // factor (in coef when shared memory is too small); X = R^-1 (in Rinv)
-    extern __shared__ float chol_smem[];
-    float *R = coef;
-    if (use_smem) {
-        A = chol_smem;
-        R = chol_smem + (size_t)p * p;
-        Rinv = chol_smem + (size_t)2 * p * p;
-    }
-    // thread (tx, ty) of a 32 x 16 grid owns the elements (ty + 16 i, tx + 32 j):
-    // no index division in the p steps below
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    __shared__ double trace;
-    if (threadIdx.x < 32) {
-        double tr = 0.0;
-        for (int i = tx; i < p; i += 32) tr += G[(long long)i * p + i];
-        tr = warp_sum(tr);
-        if (tx == 0) trace = tr;
-    }
-    __syncthreads();
-    for (int r = ty; r < p; r += 16)
-        for (int c = tx; c < p; c += 32) A[r * p + c] = (float)(G[(long long)r * p + c] + (r == c ? shift * trace : 0.0));
-    __syncthreads();
-    // right-looking factorisation, one barrier per step: row j of R is
-    // written from the unscaled row j, which the trailing update reads
-    for (int j = 0; j < p; ++j) {
-        float dj = A[j * p + j];
-        if (!(dj > 0.f) || !isfinite(dj)) {
-            if (threadIdx.x == 0) *flag = 2;
-            dj = 1.f;
-        }
-        const float rs = rsqrtf(dj), invd = 1.f / dj;
-        for (int r = ty; r < p; r += 16) {
-            if (r < j) continue;
-            for (int c = tx; c < p; c += 32) {
-                if (c < r) continue;
-                if (r == j) {
-                    R[j * p + c] = c == j ? dj * rs : A[j * p + c] * rs;
-                } else {
-                    A[r * p + c] = fmaf(-A[j * p + r] * invd, A[j * p + c], A[r * p + c]);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    // X = R^-1 by the column-oriented back substitution, one barrier per
-    // step: at step i row i of X is final (B[i][c] / R[i][i]) and removed
-    // from the rows above
-    for (int r = ty; r < p; r += 16)
-        for (int c = tx; c < p; c += 32) A[r * p + c] = r == c ? 1.f : 0.f;
-    __syncthreads();
-    for (int i = p - 1; i >= 0; --i) {
-        const float rii = 1.f / R[i * p + i];
-        for (int r = ty; r <= i; r += 16)
-            for (int c = tx; c < p; c += 32) {
-                if (c < i) continue;
-                const float xi = A[i * p + c] * rii;
-                if (r == i)
-                    Rinv[i * p + c] = xi;
-                else
-                    A[r * p + c] = fmaf(-R[r * p + i], xi, A[r * p + c]);
-            }
-        __syncthreads();
-    }
-    for (int a = ty; a < p; a += 16)
-        for (int b = tx; b < p; b += 32) coef[a * p + b] = b <= a ? Rinv[b * p + a] : 0.f;   // (R^-T)[a][b]
+    const int j = blockIdx.x * 32 + threadIdx.x, i = blockIdx.y;
+    if (j >= N || i >= M) return;
+    const TA *a = A + (long long)i * ar;
+    const double *b = B + (long long)j * bc;
+    double acc = 0.0;
+    for (int l = 0; l < K; ++l) acc = fma((double)a[(long long)l * ac], b[(long long)l * br], acc);
+    if (out) out[(long long)i * ldo + j] = acc;
+    if (outf) outf[(long long)i * ldo + j] = (float)acc;
 }
 
 // Block-cooperative cyclic Jacobi for a symmetric p x p matrix A (row-major,
@@ -444,9 +435,13 @@ __device__ void block_jacobi(T *A, T *U, int p, T *cs, short *pairs, int max_swe
 // spanning them; the returned coef [r][p] gives Q1 = coef E (zero columns for
 // the rows not taken).  An FP32 block carries ~1e-7 relative rounding, so
 // directions far below the largest are noise: taking them would amplify
-// that rounding by s_max / s_i.  work: >= 3 p^2 doubles + p ints.
+// that rounding by s_max / s_i.  With tol = 0 on a nearly orthonormal
+// block's Gram matrix the kernel is one CholeskyQR pass (every row is taken;
+// the pivoting only reorders them).  Each step's pivot takes one reciprocal
+// square root (its reciprocal is kept for the inverse), so neither loop
+// holds a division.  work: >= 3 p^2 + 2 p doubles.
 __global__ void __launch_bounds__(512) gram_pivchol_kernel(const double *__restrict__ G, int p, double tol, double *work,
-                                    float *__restrict__ coef, int *__restrict__ r_out, int *__restrict__ flag,
+                                    double *__restrict__ coef, int *__restrict__ r_out, int *__restrict__ flag,
                                     int use_smem)
 {
     extern __shared__ double smem_work[];
@@ -456,8 +451,9 @@ __global__ void __launch_bounds__(512) gram_pivchol_kernel(const double *__restr
     const long long pp = (long long)p * p;
     double *A = work, *R = A + pp, *Ri = R + pp;
     int *piv = reinterpret_cast<int *>(Ri + pp);
+    double *rinv = Ri + pp + p;                         // 1 / R_jj
     __shared__ int s_r, s_go;
-    __shared__ double s_d, s_d0;
+    __shared__ double s_dinv, s_d0;
     for (long long q = t; q < pp; q += nt) {
         A[q] = G[q];
         R[q] = 0.0;
@@ -503,8 +499,10 @@ __global__ void __launch_bounds__(512) gram_pivchol_kernel(const double *__restr
                     const int tmp = piv[j];
                     piv[j] = piv[best];
                     piv[best] = tmp;
-                    s_d = sqrt(bv);
-                    R[(long long)j * p + j] = s_d;
+                    const double di = rsqrt(bv);
+                    R[(long long)j * p + j] = bv * di;
+                    rinv[j] = di;
+                    s_dinv = di;
                     s_go = 1;
                 }
             }
@@ -514,7 +512,7 @@ __global__ void __launch_bounds__(512) gram_pivchol_kernel(const double *__restr
         // row j of R and the trailing update in one pass (neither touches
         // row or column piv[j] of A, which both read)
         const int pj = piv[j];
-        const double dinv = 1.0 / s_d;
+        const double dinv = s_dinv;
         const double *Aj = A + (long long)pj * p;
         for (int k = j + 1 + t; k < p; k += nt) R[(long long)j * p + k] = Aj[piv[k]] * dinv;
         for (int kk = j + 1 + ty; kk < p; kk += 16) {
@@ -535,7 +533,7 @@ __global__ void __launch_bounds__(512) gram_pivchol_kernel(const double *__restr
         }
     __syncthreads();
     for (int i = r - 1; i >= 0; --i) {
-        const double rii = 1.0 / R[(long long)i * p + i];
+        const double rii = rinv[i];
         for (int a = ty; a <= i; a += 16)
             for (int c = tx; c < r; c += 32) {
                 if (c < i) continue;
@@ -547,12 +545,12 @@ __global__ void __launch_bounds__(512) gram_pivchol_kernel(const double *__restr
             }
         __syncthreads();
     }
-    for (long long q = t; q < (long long)r * p; q += nt) coef[q] = 0.f;
+    for (long long q = t; q < pp; q += nt) coef[q] = 0.0;
     __syncthreads();
     // coef[a][piv[b]] = (R11^-T)[a][b] = R11^-1[b][a]
     for (int q = t; q < r * r; q += nt) {
         const int a = q / r, b = q % r;
-        coef[(long long)a * p + piv[b]] = (float)Ri[(long long)b * r + a];
+        coef[(long long)a * p + piv[b]] = Ri[(long long)b * r + a];
     }
     if (t == 0) *r_out = r;
 }
@@ -753,11 +751,10 @@ __global__ void gram_scale_kernel(double *__restrict__ G, int m, double *__restr
     for (int q = threadIdx.x; q < m * m; q += blockDim.x) G[q] *= d[q / m] * d[q % m];
 }
 
-// coef [r][m] <- coef D (undo the column scaling in the combination)
-__global__ void coef_colscale_kernel(float *__restrict__ coef, int r, int m, const double *__restrict__ d)
+// c [r][m] <- c D (undo the column scaling of the Gram matrix)
+__global__ void colscale_kernel(double *__restrict__ c, int r, int m, const double *__restrict__ d)
 {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < r * m; q += gridDim.x * blockDim.x)
-        coef[q] = (float)((double)coef[q] * d[q % m]);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < r * m; q += gridDim.x * blockDim.x) c[q] *= d[q % m];
 }
 
 // T <- (T + T^T) / 2 in place, r x r, one CTA
@@ -769,32 +766,6 @@ __global__ void sym_kernel(double *__restrict__ T, int r)
         const double v = 0.5 * (T[(long long)i * r + j] + T[(long long)j * r + i]);
         T[(long long)i * r + j] = v;
         T[(long long)j * r + i] = v;
-    }
-}
-
-// T = C M C^T (symmetrised), C [r][m], M [m][m] symmetric, FP64, one CTA;
-// P [r][m] scratch
-__global__ void exact_t_kernel(const double *__restrict__ C, const double *__restrict__ M, int r, int m,
-                               double *__restrict__ P, double *__restrict__ T)
-{
-    for (int q = threadIdx.x; q < r * m; q += blockDim.x) {
-        const int a = q / m, c = q % m;
-        double acc = 0.0;
-        for (int b = 0; b < m; ++b) acc += C[(long long)a * m + b] * M[(long long)b * m + c];
-        P[q] = acc;
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < r * r; q += blockDim.x) {
-        const int a = q / r, b = q % r;
-        if (b < a) continue;
-        double ab = 0.0, ba = 0.0;
-        for (int c = 0; c < m; ++c) {
-            ab += P[(long long)a * m + c] * C[(long long)b * m + c];
-            ba += P[(long long)b * m + c] * C[(long long)a * m + c];
-        }
-        const double v = 0.5 * (ab + ba);
-        T[(long long)a * r + b] = v;
-        T[(long long)b * r + a] = v;
     }
 }
 
@@ -1048,8 +1019,8 @@ int apply_dev(gbfwi_bfgs *h, const float *Xd, long long ldx, int p, float *Zd, l
     } else {
         GB_TRY(atb(h, h->S.as<float>(), h->BY.as<float>(), k, 2 * k, Xd, nullptr, p, p, T, p, s));
     }
-    middle_kernel<<<p, 32, 0, s>>>(T, h->dSY.as<double>(), h->dYBY.as<double>(), k, h->kmax, p, gamma, scr,
-                                   h->coef.as<float>());
+    middle_kernel<<<p, 32, (size_t)k * sizeof(double), s>>>(T, h->dSY.as<double>(), h->dYBY.as<double>(), k,
+                                                            h->kmax, p, gamma, scr, h->coef.as<float>(), nullptr);
     GB_LAUNCHED();
     return combine(h, h->S.as<float>(), h->BY.as<float>(), k, 2 * k, h->coef.as<float>(), p, Zd, ldz,
                    h->B0.as<float>(), Xd, ldx, beta, s);
@@ -1082,6 +1053,9 @@ extern "C" int gbfwi_bfgs_create(long long n, int kmax, const float *B0, gbfwi_b
     if (rc) { delete h; return rc; }
     h->SY.assign((size_t)kmax * kmax, 0.0);
     h->YBY.assign((size_t)kmax * kmax, 0.0);
+    h->SS.assign((size_t)kmax * kmax, 0.0);
+    h->SB.assign((size_t)kmax * kmax, 0.0);
+    h->BB.assign((size_t)kmax * kmax, 0.0);
     // the row padding stays zero
     if (cudaMemset(h->S.p, 0, store) != cudaSuccess || cudaMemset(h->Y.p, 0, store) != cudaSuccess ||
         cudaMemset(h->BY.p, 0, store) != cudaSuccess || cudaMemset(h->status.p, 0, 16) != cudaSuccess ||
@@ -1117,31 +1091,59 @@ extern "C" int gbfwi_bfgs_update(gbfwi_bfgs *h, const float *s_, const float *y_
     GB_CUDA(cudaMemcpyAsync(yk, y_, n * sizeof(float), cudaMemcpyDefault, s));
     mul_kernel<<<grid_n(n), 256, 0, s>>>(h->B0.as<float>(), yk, n, byk);
     GB_LAUNCHED();
-    // dots: s_i^T [y_k, s_k] (i <= k), (B0 y_i)^T y_k (i <= k), y_k^T y_k
-    GB_TRY(reserve(h, 1, false, {{k + 1, 1}}));
-    double *d1 = h->small.as<double>();          // [(k+1)][2]
-    double *d2 = d1 + 2 * (k + 1);               // [(k+1)]
-    double *d3 = d2 + (k + 1);                   // [1]
+    // dots of the new pair with the store: rows [S_0..S_k, B0Y_0..B0Y_k]
+    // against (y_k, s_k, B0 y_k), and y_k^T y_k; they extend S^T Y, Y^T B0 Y
+    // and the Gram matrix W^T W of W = [S, B0 Y]
+    const int k1 = k + 1;
+    const long long nsplit = thin_splits(n);
+    const long long chunk = (n + nsplit - 1) / nsplit;
+    const long long ns = (n + chunk - 1) / chunk;
+    GB_TRY(reserve(h, 1, false, {{k1, 1}}));
+    GB_TRY(h->part.ensure(std::max(h->part.bytes, (size_t)ns * 6 * k1 * sizeof(double))));
+    GB_TRY(h->small.ensure(std::max(h->small.bytes, (size_t)(6 * k1 + 8) * sizeof(double))));
+    double *d1 = h->small.as<double>();          // [2 k1][3]
+    double *d3 = d1 + 6 * k1;                    // [1]
     const float *S = h->S.as<float>(), *BY = h->BY.as<float>();
-    GB_TRY(atb(h, S, nullptr, k + 1, k + 1, yk, nullptr, 1, 1, d1, 2, s));
-    GB_TRY(atb(h, S, nullptr, k + 1, k + 1, sk, nullptr, 1, 1, d1 + 1, 2, s));
-    GB_TRY(atb(h, BY, nullptr, k + 1, k + 1, yk, nullptr, 1, 1, d2, 1, s));
+    pair_dots_kernel<<<dim3((unsigned)ns, (unsigned)(2 * k1)), 256, 0, s>>>(S, BY, ld, k1, yk, sk, byk, n, chunk,
+                                                                          h->part.as<double>());
+    GB_LAUNCHED();
+    atb_reduce<<<(6 * k1 + 255) / 256, 256, 0, s>>>(h->part.as<double>(), (int)ns, 6 * k1, d1, 3, 3);
+    GB_LAUNCHED();
     GB_TRY(atb(h, yk, nullptr, 1, 1, yk, nullptr, 1, 1, d3, 1, s));
-    std::vector<double> hd(4 * (k + 1) + 1);
+    std::vector<double> hd(6 * k1 + 1);
     GB_CUDA(cudaMemcpyAsync(hd.data(), d1, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
-    double ys = hd[2 * k], ss = hd[2 * k + 1], yy = hd[2 * (k + 1) + (k + 1)];
+    // hd[3 a + b]: a < k1 row s_a, a >= k1 row B0 y_(a - k1); b: y_k, s_k, B0 y_k
+    double ys = hd[3 * k], ss = hd[3 * k + 1], yy = hd[6 * k1];
     if (!std::isfinite(ys) || !std::isfinite(ss) || !std::isfinite(yy)) return gb_nonfinite("BFGS pair dot product");
     if (!(ys > 1e-12 * std::sqrt(ss) * std::sqrt(yy))) return GBFWI_ECURV;
+    for (double v : hd)
+        if (!std::isfinite(v)) return gb_nonfinite("BFGS pair dot product");
     const int km = h->kmax;
+    auto at = [km](std::vector<double> &A, int i, int j) -> double & { return A[(size_t)i * km + j]; };
     for (int i = 0; i <= k; ++i) {
-        h->SY[(size_t)i * km + k] = hd[2 * i];
-        double v = hd[2 * (k + 1) + i];
-        h->YBY[(size_t)i * km + k] = v;
-        h->YBY[(size_t)k * km + i] = v;
+        const double *sr = &hd[3 * i], *br = &hd[3 * (k1 + i)];
+        at(h->SY, i, k) = sr[0];
+        at(h->YBY, i, k) = at(h->YBY, k, i) = br[0];
+        at(h->SS, i, k) = at(h->SS, k, i) = sr[1];
+        at(h->SB, i, k) = sr[2];                     // s_i^T B0 y_k
+        if (i < k) at(h->SB, k, i) = br[1];          // s_k^T B0 y_i
+        at(h->BB, i, k) = at(h->BB, k, i) = br[2];
     }
     GB_CUDA(cudaMemcpyAsync(h->dSY.p, h->SY.data(), h->SY.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     GB_CUDA(cudaMemcpyAsync(h->dYBY.p, h->YBY.data(), h->YBY.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    // W^T W for the k1 pairs: [[S^T S, S^T B0 Y], [(S^T B0 Y)^T, (B0 Y)^T B0 Y]]
+    const int m1 = 2 * k1;
+    std::vector<double> Gm((size_t)m1 * m1);
+    for (int a = 0; a < k1; ++a)
+        for (int b = 0; b < k1; ++b) {
+            Gm[(size_t)a * m1 + b] = at(h->SS, a, b);
+            Gm[(size_t)a * m1 + k1 + b] = at(h->SB, a, b);
+            Gm[(size_t)(k1 + b) * m1 + a] = at(h->SB, a, b);
+            Gm[(size_t)(k1 + a) * m1 + k1 + b] = at(h->BB, a, b);
+        }
+    GB_TRY(h->dG.ensure(Gm.size() * sizeof(double)));
+    GB_CUDA(cudaMemcpyAsync(h->dG.p, Gm.data(), Gm.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     GB_CUDA(cudaStreamSynchronize(s));
     h->k = k + 1;
     return GBFWI_OK;
@@ -1183,16 +1185,178 @@ extern "C" int gbfwi_bfgs_apply(gbfwi_bfgs *h, const float *X, int p, float *Z, 
 
 namespace {
 
+// Sequential carve-up of the FP64 scratch of a decomposition
+struct Arena {
+    double *base;
+    size_t off = 0;
+    double *take(size_t n)
+    {
+        double *q = base + off;
+        off += (n + 7) / 8 * 8;          // keep every piece 64-byte aligned
+        return q;
+    }
+};
+
+// FP64 scratch doubles of a decomposition with p probes (or basis rows) and m = 2k
+size_t lowrank_doubles(int p, int m)
+{
+    const size_t P = (size_t)std::max(p, m), pm = P * (size_t)m, pp = P * P;
+    return 12 * pm + 20 * pp + (size_t)m * m + 16 * P + 1024;
+}
+
+// out (M x N, row stride ldo) = A(i, l) B(l, j) over K, see small_gemm_kernel
+template <typename TA>
+int gemm(int M, int N, int K, const TA *A, long long ar, long long ac, const double *B, long long br, long long bc,
+         double *out, float *outf, long long ldo, cudaStream_t s)
+{
+    if (M < 1 || N < 1) return GBFWI_OK;
+    small_gemm_kernel<TA><<<dim3((unsigned)((N + 31) / 32), (unsigned)M), 32, 0, s>>>(M, N, K, A, ar, ac, B, br, bc,
+                                                                                    out, outf, ldo);
+    GB_LAUNCHED();
+    return GBFWI_OK;
+}
+
+int launch_pivchol(const double *G, int p, double tol, double *work, double *coef, int *r_out, int *flag,
+                   cudaStream_t s)
+{
+    const size_t ws = (3 * (size_t)p * p + 2 * (size_t)p) * sizeof(double);
+    const int use_smem = ws <= 200 * 1024;
+    if (use_smem)
+        GB_CUDA(cudaFuncSetAttribute(gram_pivchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
+    gram_pivchol_kernel<<<1, 512, use_smem ? ws : 0, s>>>(G, p, tol, work, coef, r_out, flag, use_smem);
+    GB_LAUNCHED();
+    return GBFWI_OK;
+}
+
+int launch_eig(const double *T, int r, int rank, double *work, double *lam, float *coef, int *flag, cudaStream_t s)
+{
+    const size_t we = ((size_t)r * r + r + 16 + ((size_t)r + 2) * (r + 2) / 4) * sizeof(double);
+    const int use_smem = we <= 200 * 1024;
+    if (use_smem)
+        GB_CUDA(cudaFuncSetAttribute(eig_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)we));
+    eig_select_kernel<<<1, 512, use_smem ? we : 0, s>>>(T, r, rank, work, lam, coef, flag, use_smem);
+    GB_LAUNCHED();
+    return GBFWI_OK;
+}
+
+// Every block of the decompositions lies in the span of the rows of W =
+// [S, B0 Y] (m = 2k rows): E = (B - B0) X = C W with C = (M W^T X)^T, M the
+// middle matrix of the compact form (gamma = 1), and so does every basis
+// built from E.  The decompositions therefore carry their bases as FP64
+// coordinates T ([r][m], basis = T W) and form every Gram matrix and
+// projection from G = W^T W (kept by the update), W^T X and M in FP64:
+//   E E^T = C G C^T,  Q Q^T = T G T^T,  Q E^T = T G C^T,  Q X^T = T (W^T X),
+//   Q (B - B0) Q^T = (G T^T)^T M (G T^T).
+// The n-long work is the one product W^T X and the final combination
+// V = (U^T T) W; the FP32 rounding of E, of the basis and of its
+// re-orthogonalisations never happens.
+//
+// The orthonormal basis of a block with coordinates Cb ([q][m]) and Gram
+// matrix Gb = Cb G Cb^T: rank-revealing pivoted Cholesky of Gb (rows kept
+// while their residual norm is >= tol of the largest), T1 = coef1 Cb, then
+// one CholeskyQR pass in FP64 (pivoted Cholesky of T1 G T1^T with tol 0),
+// Tq = coef2 T1.  Returns r through *r_host after one synchronisation;
+// r_dev[1] holds the second pass's count (equal to r unless that Gram
+// matrix lost definiteness, checked at the end).
+int basis_coords(gbfwi_bfgs *h, const double *Gb, const double *Cb, int q, int m, double tol, const double *colscale,
+                 Arena &ar, double *&Tq, int &r, int *r_dev, int *flag, cudaStream_t s)
+{
+    const double *G = h->dG.as<double>();
+    const size_t P = (size_t)std::max(q, m);
+    double *work = ar.take(3 * P * P + 2 * P);
+    double *c1 = ar.take(P * P), *c2 = ar.take(P * P), *Gq = ar.take(P * P);
+    double *T1 = ar.take(P * m), *P2 = ar.take(P * m);
+    Tq = ar.take(P * m);
+    GB_TRY(launch_pivchol(Gb, q, tol, work, c1, r_dev, flag, s));
+    GB_CUDA(cudaMemcpyAsync(&r, r_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    GB_TRY(take_status(h));
+    if (r < 1) return GBFWI_OK;
+    if (colscale) {
+        // Cb = D (identity coordinates, scaled Gram matrix): T1 = coef1 D
+        GB_CUDA(cudaMemcpyAsync(T1, c1, (size_t)r * m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        colscale_kernel<<<std::max(1, (r * m + 255) / 256), 256, 0, s>>>(T1, r, m, colscale);
+        GB_LAUNCHED();
+    } else {
+        GB_TRY(gemm(r, m, q, c1, q, 1, Cb, m, 1, T1, nullptr, m, s));          // T1 = coef1 Cb
+    }
+    GB_TRY(gemm(r, m, m, T1, m, 1, G, m, 1, P2, nullptr, m, s));               // P2 = T1 G
+    GB_TRY(gemm(r, r, m, P2, m, 1, T1, 1, m, Gq, nullptr, r, s));              // Gq = P2 T1^T
+    GB_TRY(launch_pivchol(Gq, r, 0.0, work, c2, r_dev + 1, flag, s));
+    GB_TRY(gemm(r, m, r, c2, r, 1, T1, m, 1, Tq, nullptr, m, s));              // Tq = coef2 T1
+    return GBFWI_OK;
+}
+
+// The Rayleigh-Ritz matrix of the basis Tq W, Q (B - B0) Q^T = Y^T M Y with
+// Y = G Tq^T ([m][r]), symmetrised into Cm [r][r]
+int rayleigh_ritz(gbfwi_bfgs *h, const double *Tq, int r, int m, Arena &ar, double *Cm, cudaStream_t s)
+{
+    const int k = h->k;
+    const double *G = h->dG.as<double>();
+    double *Yc = ar.take((size_t)m * r), *CdY = ar.take((size_t)r * m), *mid = ar.take((size_t)r * m);
+    GB_TRY(gemm(m, r, m, G, m, 1, Tq, 1, m, Yc, nullptr, r, s));               // Y = G Tq^T
+    middle_kernel<<<r, 32, (size_t)k * sizeof(double), s>>>(Yc, h->dSY.as<double>(), h->dYBY.as<double>(), k,
+                                                            h->kmax, r, 1.0, mid, nullptr, CdY);   // (M Y)^T
+    GB_LAUNCHED();
+    GB_TRY(gemm(r, r, m, CdY, m, 1, Yc, r, 1, Cm, nullptr, r, s));             // Y^T M Y
+    sym_kernel<<<1, 256, 0, s>>>(Cm, r);
+    GB_LAUNCHED();
+    return GBFWI_OK;
+}
+
+// V = (U^T Tq) W for the first `rank` eigenvectors (coef = U^T, [rank][r];
+// rows beyond r are zero), then the posterior std (Eq. 14) and the copies out
+int finish_lowrank(gbfwi_bfgs *h, const double *Tq, int r, int rank, const double *lam, double eps_prior, float *V,
+                   double *lambda, float *std_out, Arena &ar, const int *flag, const int *r_dev, cudaStream_t s)
+{
+    const long long n = h->n, ld = h->ld;
+    const int k = h->k, m = 2 * k;
+    float *F = reinterpret_cast<float *>(ar.take(((size_t)rank * m + 1) / 2));
+    GB_TRY(gemm(rank, m, r, h->coef.as<float>(), r, 1, Tq, m, 1, (double *)nullptr, F, m, s));
+    GB_TRY(h->E.ensure((size_t)std::max(rank, 1) * ld * sizeof(float)));
+    GB_TRY(h->Q.ensure((size_t)ld * sizeof(float)));
+    const bool devV = V && gb_is_device_ptr(V);
+    float *Vd = devV ? V : h->E.as<float>();
+    const long long ldv = devV ? n : ld;
+    GB_TRY(combine(h, h->S.as<float>(), h->BY.as<float>(), k, m, F, rank, Vd, ldv, nullptr, nullptr, 0, 0.f, s));
+    if (std_out) {
+        const bool devS = gb_is_device_ptr(std_out);
+        float *Sd = devS ? std_out : h->Q.as<float>();
+        std_kernel<<<grid_n(n), 256, 0, s>>>(Vd, ldv, lam, rank, h->B0.as<float>(), n, (float)eps_prior, Sd);
+        GB_LAUNCHED();
+        if (!devS) GB_CUDA(cudaMemcpyAsync(std_out, Sd, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    }
+    if (V && !devV) GB_TRY(unstage_rows(h, V, Vd, rank, s));
+    if (lambda)
+        GB_CUDA(cudaMemcpyAsync(lambda, lam, rank * sizeof(double),
+                                gb_is_device_ptr(lambda) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    int fl[3] = {0, 0, 0};
+    GB_CUDA(cudaMemcpyAsync(fl, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(fl + 1, r_dev + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    GB_TRY(take_status(h));
+    int flag_h = fl[0];
+    if (!flag_h && fl[1] != r) flag_h = 2;            // the CholeskyQR pass lost a row
+    if (flag_h) {
+        static const char *stage[] = {"", "Gram matrix of the block", "Cholesky pivot of the basis Gram matrix",
+                                      "singular Q^T X", "eigenvalues of the projected matrix"};
+        return gb_nonfinite(stage[flag_h >= 1 && flag_h <= 4 ? flag_h : 0]);
+    }
+    return GBFWI_OK;
+}
+
 // The randomized eigendecomposition of B_{n+1} - B0 (Algorithm 3): probes
 // X (given, or Philox normals), E = (B - B0) X, a rank-revealing orthonormal
 // basis Q of E's rows; then either the single pass of Algorithm 3 (Omega
 // from Omega (Q^T X) = Q^T E) or, two_pass, the Rayleigh-Ritz second pass
 // C = Q (B - B0) Q^T.  Eigenpairs, V = U^T Q and the posterior std follow.
+// All of it in the coordinates of W = [S, B0 Y] (see basis_coords).
 int lowrank_randomized(gbfwi_bfgs *h, const float *X, int p, int rank, unsigned long long seed, double eps_prior,
                        float *V, double *lambda, float *std_out, bool two_pass, cudaStream_t s)
 {
     const long long n = h->n, ld = h->ld;
-    const int k = h->k;
+    const int k = h->k, m = 2 * k;
+    if (k < 1) return gb_nonfinite("probe block E = (B - B0) X is zero or not finite");
     // the probe block in a store buffer (aligned rows for the tensor cores)
     if (X) {
         GB_TRY(stage_rows(h, h->X, X, p, s));
@@ -1202,64 +1366,37 @@ int lowrank_randomized(gbfwi_bfgs *h, const float *X, int p, int rank, unsigned 
         GB_LAUNCHED();
     }
     const float *Xd = h->X.as<float>();
-    GB_TRY(h->E.ensure((size_t)p * ld * sizeof(float)));
-    GB_TRY(h->Q.ensure((size_t)p * ld * sizeof(float)));
-    GB_TRY(h->V.ensure((size_t)p * ld * sizeof(float)));
-    GB_TRY(reserve(h, p, true, {{2 * k, p}, {p, p}, {p, 2 * p}}));
-    float *E = h->E.as<float>(), *Q = h->Q.as<float>();
-    // 1. E = (B_{n+1} - B0) X
-    GB_TRY(apply_dev(h, Xd, ld, p, E, ld, 1.0, 1, s));
-    // 2. rank-revealing basis of E: pivoted Cholesky of its FP64 Gram matrix,
-    //    rows kept while their residual norm is >= 1e-4 of the largest (what an
-    //    FP32 block resolves)
-    const size_t pp = (size_t)p * p;
-    double *G = h->small.as<double>() + small_apply_doubles(h, p);
-    double *A = G + pp, *R2 = A + pp, *Rinv = R2 + pp, *QEX = Rinv + pp;   // QEX: [p][2p]
-    double *work = QEX + 2 * pp;          // 4 pp + 4 p
-    double *lam = work + 4 * pp + 4 * (size_t)p;
-    int *rdev = reinterpret_cast<int *>(lam + p + 2);
-    float *coef = h->coef.as<float>();
+    GB_TRY(reserve(h, p, false, {{m, p}}));
+    GB_TRY(h->ex.ensure(lowrank_doubles(p, m) * sizeof(double)));
+    Arena ar{h->ex.as<double>()};
+    const size_t pm = (size_t)p * m, pp = (size_t)p * p;
+    double *Z = ar.take(pm), *Cd = ar.take(pm), *Pm = ar.take(pm), *mid = ar.take(pm), *Ge = ar.take(pp);
+    double *lam = ar.take((size_t)p + 2);
+    int *rdev = reinterpret_cast<int *>(ar.take(2));
     int *flag = h->flag.as<int>();
+    const double *G = h->dG.as<double>();
     GB_CUDA(cudaMemsetAsync(flag, 0, 16, s));
-    const size_t ws = (4 * pp + 4 * (size_t)p) * sizeof(double);
-    const int use_smem = ws <= 200 * 1024;
-    if (use_smem) {
-        GB_CUDA(cudaFuncSetAttribute(gram_pivchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
-    }
-    GB_TRY(atb(h, E, nullptr, p, p, E, nullptr, p, p, G, p, s));
-    gram_pivchol_kernel<<<1, 512, use_smem ? ws : 0, s>>>(G, p, 1e-4, work, coef, rdev, flag, use_smem);
+    // 1. Z = W^T X (one pass over S, B0 Y and X), C = (M Z)^T: E = C W
+    GB_TRY(atb(h, h->S.as<float>(), h->BY.as<float>(), k, m, Xd, nullptr, p, p, Z, p, s));
+    middle_kernel<<<p, 32, (size_t)k * sizeof(double), s>>>(Z, h->dSY.as<double>(), h->dYBY.as<double>(), k, h->kmax,
+                                                            p, 1.0, mid, nullptr, Cd);
     GB_LAUNCHED();
+    // 2. E E^T = C G C^T, the basis coordinates Tq
+    GB_TRY(gemm(p, m, m, Cd, m, 1, G, m, 1, Pm, nullptr, m, s));               // P = C G
+    GB_TRY(gemm(p, p, m, Pm, m, 1, Cd, 1, m, Ge, nullptr, p, s));              // E E^T = P C^T
+    double *Tq = nullptr;
     int r = 0;
-    GB_CUDA(cudaMemcpyAsync(&r, rdev, sizeof(int), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaStreamSynchronize(s));
-    GB_TRY(take_status(h));
+    GB_TRY(basis_coords(h, Ge, Cd, p, m, 1e-4, nullptr, ar, Tq, r, rdev, flag, s));
     if (r < 1) return gb_nonfinite("probe block E = (B - B0) X is zero or not finite");
-    GB_TRY(combine(h, E, nullptr, p, p, coef, r, Q, ld, nullptr, nullptr, 0, 0.f, s));   // Q1 [r] rows in Q
-    // shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa
-    // 2020): Q1 is orthonormal only up to its FP32 rounding times cond(R11),
-    // and its FP32 Gram matrix may then miss definiteness; the first pass
-    // adds 1e-5 tr(G) to the diagonal (well above the Gram's rounding), the
-    // two unshifted passes make the rows orthonormal to FP32 rounding
-    float *Qf = h->V.as<float>();
-    const size_t wc = (size_t)3 * r * r * sizeof(float);
-    const int chol_smem = wc <= 200 * 1024;
-    if (chol_smem) GB_CUDA(cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wc));
-    for (int pass = 0; pass < 3; ++pass) {
-        GB_TRY(atb(h, Q, nullptr, r, r, Q, nullptr, r, r, G, r, s));
-        chol_kernel<<<1, 512, chol_smem ? wc : 0, s>>>(G, r, pass == 0 ? 1e-5 : 0.0, reinterpret_cast<float *>(A),
-                                                       reinterpret_cast<float *>(Rinv), coef, flag, chol_smem);
-        GB_LAUNCHED();
-        GB_TRY(combine(h, Q, nullptr, r, r, coef, r, Qf, ld, nullptr, nullptr, 0, 0.f, s));
-        std::swap(Q, Qf);                 // Q: current basis; Qf: free
-    }
-    std::swap(Q, Qf);                     // Qf: the basis; Q: free
+    double *work = ar.take(4 * pp + 4 * (size_t)p);
+    double *Om = ar.take(pp);
     if (!two_pass) {
-        // 3. [Q^T E, Q^T X] in one pass over Q (Omega = (Q^T E)(Q^T X)^-1
-        //    amplifies their error by cond(Q^T X)); Omega by least squares; eigenpairs
-        GB_TRY(atb(h, Qf, nullptr, r, r, E, Xd, p, 2 * p, QEX, 2 * p, s));
-        // N (in A), Bm^T (in G), N = P^T L U (U in A, L in R2), Omega^T (in Rinv)
+        // 3. [Q^T E, Q^T X] (Q E^T = Tq P^T, Q X^T = Tq Z), Omega by least squares
+        double *QEX = ar.take(2 * pp), *A = ar.take(pp), *Bm = ar.take(pp), *R2 = ar.take(pp);
+        GB_TRY(gemm(r, p, m, Tq, m, 1, Pm, 1, m, QEX, nullptr, 2 * p, s));
+        GB_TRY(gemm(r, p, m, Tq, m, 1, Z, p, 1, QEX + p, nullptr, 2 * p, s));
         int *perm = reinterpret_cast<int *>(work + pp);
-        omega_system_kernel<<<r, 32, 0, s>>>(QEX, QEX + p, 2 * p, r, p, A, G);
+        omega_system_kernel<<<r, 32, 0, s>>>(QEX, QEX + p, 2 * p, r, p, A, Bm);
         GB_LAUNCHED();
         const size_t wl = (size_t)2 * r * r * sizeof(double);
         const int lu_smem = wl <= 200 * 1024;
@@ -1267,57 +1404,16 @@ int lowrank_randomized(gbfwi_bfgs *h, const float *X, int p, int rank, unsigned 
         lu_kernel<<<1, 512, lu_smem ? wl : 0, s>>>(A, R2, perm, r, flag, lu_smem);
         GB_LAUNCHED();
         if (lu_smem) GB_CUDA(cudaFuncSetAttribute(lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wl));
-        lu_solve_kernel<<<r, 32, lu_smem ? wl : 0, s>>>(A, R2, perm, G, r, Rinv, lu_smem);
+        lu_solve_kernel<<<r, 32, lu_smem ? wl : 0, s>>>(A, R2, perm, Bm, r, Om, lu_smem);
         GB_LAUNCHED();
-        sym_kernel<<<1, 512, 0, s>>>(Rinv, r);
-        GB_LAUNCHED();
-        const size_t we = ((size_t)r * r + r + 16 + ((size_t)r + 2) * (r + 2) / 4) * sizeof(double);
-        const int use_smem2 = we <= 200 * 1024;
-        if (use_smem2)
-            GB_CUDA(cudaFuncSetAttribute(eig_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)we));
-        eig_select_kernel<<<1, 512, use_smem2 ? we : 0, s>>>(Rinv, r, rank, work, lam, coef, flag, use_smem2);
+        sym_kernel<<<1, 512, 0, s>>>(Om, r);
         GB_LAUNCHED();
     } else {
-        // 3. second pass: E2 = (B - B0) Q (into E, free now), C = Q E2^T
-        //    (the Rayleigh-Ritz matrix, symmetrised), its eigenpairs
-        GB_TRY(apply_dev(h, Qf, ld, r, E, ld, 1.0, 1, s));
-        GB_TRY(atb(h, Qf, nullptr, r, r, E, nullptr, r, r, G, r, s));
-        sym_kernel<<<1, 256, 0, s>>>(G, r);
-        GB_LAUNCHED();
-        const size_t we = ((size_t)r * r + r + 16 + ((size_t)r + 2) * (r + 2) / 4) * sizeof(double);
-        const int use_smem2 = we <= 200 * 1024;
-        if (use_smem2)
-            GB_CUDA(cudaFuncSetAttribute(eig_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)we));
-        eig_select_kernel<<<1, 512, use_smem2 ? we : 0, s>>>(G, r, rank, work, lam, coef, flag, use_smem2);
-        GB_LAUNCHED();
+        // 3. second pass: the Rayleigh-Ritz matrix Q (B - B0) Q^T
+        GB_TRY(rayleigh_ritz(h, Tq, r, m, ar, Om, s));
     }
-    // 4. V = Q U (first `rank` eigenvectors; rows beyond r are zero)
-    const bool devV = V && gb_is_device_ptr(V);
-    float *Vd = devV ? V : E;             // E buffer is free now
-    const long long ldv = devV ? n : ld;
-    GB_TRY(combine(h, Qf, nullptr, r, r, coef, rank, Vd, ldv, nullptr, nullptr, 0, 0.f, s));
-    // 5. posterior std (Eq. 14)
-    if (std_out) {
-        bool devS = gb_is_device_ptr(std_out);
-        float *Sd = devS ? std_out : Q;   // Q buffer is free now
-        std_kernel<<<grid_n(n), 256, 0, s>>>(Vd, ldv, lam, rank, h->B0.as<float>(), n, (float)eps_prior, Sd);
-        GB_LAUNCHED();
-        if (!devS) GB_CUDA(cudaMemcpyAsync(std_out, Sd, n * sizeof(float), cudaMemcpyDeviceToHost, s));
-    }
-    if (V && !devV) GB_TRY(unstage_rows(h, V, Vd, rank, s));
-    if (lambda)
-        GB_CUDA(cudaMemcpyAsync(lambda, lam, rank * sizeof(double),
-                                gb_is_device_ptr(lambda) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-    int flag_h = 0;
-    GB_CUDA(cudaMemcpyAsync(&flag_h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaStreamSynchronize(s));
-    GB_TRY(take_status(h));
-    if (flag_h) {
-        static const char *stage[] = {"", "Gram matrix of E", "Cholesky pivot of the basis Gram matrix",
-                                      "singular Q^T X", "eigenvalues of Omega"};
-        return gb_nonfinite(stage[flag_h >= 1 && flag_h <= 4 ? flag_h : 0]);
-    }
-    return GBFWI_OK;
+    GB_TRY(launch_eig(Om, r, rank, work, lam, h->coef.as<float>(), flag, s));
+    return finish_lowrank(h, Tq, r, rank, lam, eps_prior, V, lambda, std_out, ar, flag, rdev, s);
 }
 
 }  // namespace
@@ -1348,116 +1444,27 @@ extern "C" int gbfwi_lowrank_exact(gbfwi_bfgs *h, int rank, double eps_prior, fl
     const int m = 2 * k;
     if (rank < 1 || rank > m) return GBFWI_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    const long long n = h->n, ld = h->ld;
     const size_t mm = (size_t)m * m;
-    GB_TRY(reserve(h, m, true, {{m, m}}));
-    GB_TRY(h->ex.ensure((12 * mm + 4 * (size_t)m + 64) * sizeof(double)));
-    GB_TRY(h->E.ensure((size_t)m * ld * sizeof(float)));
-    GB_TRY(h->Q.ensure((size_t)m * ld * sizeof(float)));
-    GB_TRY(h->V.ensure((size_t)m * ld * sizeof(float)));
-    double *G = h->ex.as<double>();
-    double *work = G + mm;                 // 4 mm
-    double *C = work + 4 * mm, *M = C + mm, *P = M + mm, *T = P + mm;
-    double *cA = T + mm, *cR = cA + mm, *cRi = cR + mm;
-    double *d = cRi + mm, *lam = d + m;
-    int *rdev = reinterpret_cast<int *>(lam + m);
-    float *coef = h->coef.as<float>();
+    GB_TRY(reserve(h, m, false, {}));
+    GB_TRY(h->ex.ensure(lowrank_doubles(m, m) * sizeof(double)));
+    Arena ar{h->ex.as<double>()};
+    double *Gs = ar.take(mm), *d = ar.take(m), *lam = ar.take((size_t)m + 2);
+    int *rdev = reinterpret_cast<int *>(ar.take(2));
     int *flag = h->flag.as<int>();
-    const float *S = h->S.as<float>(), *BY = h->BY.as<float>();
     GB_CUDA(cudaMemsetAsync(flag, 0, 16, s));
-
-    // 1. rank-revealing basis of W = [S, B0 Y] (rows s_i, B0 y_i): pivoted
-    //    Cholesky of the column-scaled Gram matrix W^T W (one tensor-core
-    //    pass over S and B0 Y), then shifted CholeskyQR3
-    GB_TRY(atb(h, S, BY, k, m, S, BY, k, m, G, m, s));
-    gram_scale_kernel<<<1, 256, 0, s>>>(G, m, d);
+    // 1. rank-revealing basis of W = [S, B0 Y]: pivoted Cholesky of the
+    //    column-scaled Gram matrix D W^T W D (d_i = 1 / |w_i|), coordinates
+    //    coef1 D, then a CholeskyQR pass (no n-long work: G is kept by the update)
+    GB_CUDA(cudaMemcpyAsync(Gs, h->dG.p, mm * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    gram_scale_kernel<<<1, 256, 0, s>>>(Gs, m, d);
     GB_LAUNCHED();
-    const size_t ws = (3 * mm + (size_t)m) * sizeof(double);
-    const int use_smem = ws <= 200 * 1024;
-    if (use_smem)
-        GB_CUDA(cudaFuncSetAttribute(gram_pivchol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws));
-    gram_pivchol_kernel<<<1, 512, use_smem ? ws : 0, s>>>(G, m, 1e-4, work, coef, rdev, flag, use_smem);
-    GB_LAUNCHED();
+    double *Tq = nullptr;
     int r = 0;
-    GB_CUDA(cudaMemcpyAsync(&r, rdev, sizeof(int), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaStreamSynchronize(s));
-    GB_TRY(take_status(h));
+    GB_TRY(basis_coords(h, Gs, nullptr, m, m, 1e-4, d, ar, Tq, r, rdev, flag, s));
     if (r < 1) return gb_nonfinite("BFGS pairs S, B0 Y are zero or not finite");
-    coef_colscale_kernel<<<grid_n((long long)r * m), 256, 0, s>>>(coef, r, m, d);
-    GB_LAUNCHED();
-    float *Qa = h->E.as<float>(), *Qb = h->Q.as<float>();
-    GB_TRY(combine(h, S, BY, k, m, coef, r, Qa, ld, nullptr, nullptr, 0, 0.f, s));
-    const size_t wc = (size_t)3 * r * r * sizeof(float);
-    const int chol_smem = wc <= 200 * 1024;
-    if (chol_smem) GB_CUDA(cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wc));
-    for (int pass = 0; pass < 3; ++pass) {   // shifted CholeskyQR3, as in gbfwi_lowrank_invhess
-        GB_TRY(atb(h, Qa, nullptr, r, r, Qa, nullptr, r, r, G, r, s));
-        chol_kernel<<<1, 512, chol_smem ? wc : 0, s>>>(G, r, pass == 0 ? 1e-5 : 0.0, reinterpret_cast<float *>(cA),
-                                                       reinterpret_cast<float *>(cRi), coef, flag, chol_smem);
-        GB_LAUNCHED();
-        GB_TRY(combine(h, Qa, nullptr, r, r, coef, r, Qb, ld, nullptr, nullptr, 0, 0.f, s));
-        std::swap(Qa, Qb);                 // Qa: current basis
-    }
-    // 2. C = Q^T W (one pass) and the middle matrix M of the compact form
-    //    (gamma = 1): B - B0 = W M W^T, M = [[R^-T (D + Y^T B0 Y) R^-1, -R^-T], [-R^-1, 0]]
-    GB_TRY(atb(h, Qa, nullptr, r, r, S, BY, k, m, C, m, s));
-    std::vector<double> Mh(mm, 0.0), Ri((size_t)k * k, 0.0);
-    {
-        const int km = h->kmax;
-        for (int c = 0; c < k; ++c)                       // R^-1 by back substitution
-            for (int i = c; i >= 0; --i) {
-                double acc = (i == c) ? 1.0 : 0.0;
-                for (int j = i + 1; j <= c; ++j) acc -= h->SY[(size_t)i * km + j] * Ri[(size_t)j * k + c];
-                Ri[(size_t)i * k + c] = acc / h->SY[(size_t)i * km + i];
-            }
-        std::vector<double> Dm((size_t)k * k), tmp((size_t)k * k, 0.0);
-        for (int i = 0; i < k; ++i)
-            for (int j = 0; j < k; ++j)
-                Dm[(size_t)i * k + j] = h->YBY[(size_t)i * km + j] + (i == j ? h->SY[(size_t)i * km + i] : 0.0);
-        for (int i = 0; i < k; ++i)                       // tmp = (D + Y^T B0 Y) R^-1
-            for (int j = 0; j < k; ++j) {
-                double acc = 0.0;
-                for (int l = 0; l < k; ++l) acc += Dm[(size_t)i * k + l] * Ri[(size_t)l * k + j];
-                tmp[(size_t)i * k + j] = acc;
-            }
-        for (int i = 0; i < k; ++i)
-            for (int j = 0; j < k; ++j) {
-                double acc = 0.0;                         // (R^-T tmp)_ij = sum_l Ri[l][i] tmp[l][j]
-                for (int l = 0; l < k; ++l) acc += Ri[(size_t)l * k + i] * tmp[(size_t)l * k + j];
-                Mh[(size_t)i * m + j] = acc;
-                Mh[(size_t)i * m + k + j] = -Ri[(size_t)j * k + i];     // -R^-T
-                Mh[(size_t)(k + i) * m + j] = -Ri[(size_t)i * k + j];   // -R^-1
-            }
-    }
-    GB_CUDA(cudaMemcpyAsync(M, Mh.data(), mm * sizeof(double), cudaMemcpyHostToDevice, s));
-    // 3. T = C M C^T, its eigenpairs, V = Q U
-    exact_t_kernel<<<1, 512, 0, s>>>(C, M, r, m, P, T);
-    GB_LAUNCHED();
-    const size_t we = ((size_t)r * r + r + 16 + ((size_t)r + 2) * (r + 2) / 4) * sizeof(double);
-    const int use_smem2 = we <= 200 * 1024;
-    if (use_smem2)
-        GB_CUDA(cudaFuncSetAttribute(eig_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)we));
-    eig_select_kernel<<<1, 512, use_smem2 ? we : 0, s>>>(T, r, rank, work, lam, coef, flag, use_smem2);
-    GB_LAUNCHED();
-    const bool devV = V && gb_is_device_ptr(V);
-    float *Vd = devV ? V : Qb;            // Qb is free
-    const long long ldv = devV ? n : ld;
-    GB_TRY(combine(h, Qa, nullptr, r, r, coef, rank, Vd, ldv, nullptr, nullptr, 0, 0.f, s));
-    if (std_out) {
-        const bool devS = gb_is_device_ptr(std_out);
-        float *Sd = devS ? std_out : h->V.as<float>();
-        std_kernel<<<grid_n(n), 256, 0, s>>>(Vd, ldv, lam, rank, h->B0.as<float>(), n, (float)eps_prior, Sd);
-        GB_LAUNCHED();
-        if (!devS) GB_CUDA(cudaMemcpyAsync(std_out, Sd, n * sizeof(float), cudaMemcpyDeviceToHost, s));
-    }
-    if (V && !devV) GB_TRY(unstage_rows(h, V, Vd, rank, s));
-    if (lambda)
-        GB_CUDA(cudaMemcpyAsync(lambda, lam, rank * sizeof(double),
-                                gb_is_device_ptr(lambda) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-    int flag_h = 0;
-    GB_CUDA(cudaMemcpyAsync(&flag_h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    GB_CUDA(cudaStreamSynchronize(s));
-    GB_TRY(take_status(h));
-    if (flag_h) return gb_nonfinite("exact low-rank decomposition of the BFGS pairs");
-    return GBFWI_OK;
+    // 2. T = Q (B - B0) Q^T = C M C^T with C = Q W^T = Tq G, its eigenpairs, V = U^T Q
+    double *work = ar.take(4 * mm + 4 * (size_t)m), *T = ar.take(mm);
+    GB_TRY(rayleigh_ritz(h, Tq, r, m, ar, T, s));
+    GB_TRY(launch_eig(T, r, rank, work, lam, h->coef.as<float>(), flag, s));
+    return finish_lowrank(h, Tq, r, rank, lam, eps_prior, V, lambda, std_out, ar, flag, rdev, s);
 }
