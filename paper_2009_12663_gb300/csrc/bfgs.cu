@@ -234,6 +234,25 @@ __global__ void mul_kernel(const float *__restrict__ a, const float *__restrict_
         out[i] = a[i] * b[i];
 }
 
+// Largest of the lanes' values (first index among equals; idx < 0: none),
+// broadcast to the warp.  The values are compared through their IEEE bit
+// patterns as signed 64-bit integers, which orders every non-negative double
+// (and puts any negative one below them): integer compares and shuffles
+// instead of FP64 compares in the pivot searches' serial steps.
+__device__ __forceinline__ void warp_argmax_nonneg(double &v, int &idx)
+{
+    long long key = __double_as_longlong(v);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const long long ok = __shfl_down_sync(0xffffffffu, key, off);
+        const int oi = __shfl_down_sync(0xffffffffu, idx, off);
+        if (oi >= 0 && (idx < 0 || ok > key || (ok == key && oi < idx))) { key = ok; idx = oi; }
+    }
+    key = __shfl_sync(0xffffffffu, key, 0);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    v = __longlong_as_double(key);
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -248,41 +267,60 @@ __device__ __forceinline__ double warp_sum(double v)
 // i.e. coef[c] = M T_c with M the middle matrix of the compact form.  One
 // warp per probe column c (block c): the k-long FP64 triangular solves and
 // the Y^T B0 Y product, dot products split over the lanes; FP64 is spread
-// over p SMs instead of one.  The reciprocals of the diagonal of R are
-// formed once, in parallel (dynamic shared memory: k doubles), so the
-// solves' dependent chains hold no division.  Outputs (either may be null):
-// coef FP32 and coefd FP64, both [p][2k].
-__global__ void __launch_bounds__(32) middle_kernel(const double *__restrict__ T, const double *__restrict__ SY,
-                                                    const double *__restrict__ YBY, int k, int kmax, int p,
-                                                    double gamma, double *__restrict__ scratch,
-                                                    float *__restrict__ coef, double *__restrict__ coefd)
+// over p SMs instead of one.  The solves are chains of dependent steps, so
+// everything they read sits in shared memory (middle_smem_bytes): cv, d,
+// the reciprocals of R's diagonal (formed once, in parallel: no division
+// in the chains) and, when mats, R = S^T Y and Y^T B0 Y themselves (k x k
+// each; otherwise they are read from global memory).  Outputs (either may
+// be null): coef FP32 and coefd FP64, both [p][2k].
+__host__ __device__ inline size_t middle_smem_bytes(int k, bool mats)
 {
-    extern __shared__ double rdiag[];
+    return ((mats ? 2 * (size_t)k * k : 0) + 3 * (size_t)k) * sizeof(double);
+}
+
+__global__ void __launch_bounds__(32) middle_kernel(const double *__restrict__ T, const double *__restrict__ SYg,
+                                                    const double *__restrict__ YBYg, int k, int kmax, int p,
+                                                    double gamma, int mats, float *__restrict__ coef,
+                                                    double *__restrict__ coefd)
+{
+    extern __shared__ double msm[];
     const int c = blockIdx.x, lane = threadIdx.x;
     if (c >= p) return;
-    for (int i = lane; i < k; i += 32) rdiag[i] = 1.0 / __ldg(SY + (long long)i * kmax + i);
+    double *cv = msm, *d = cv + k, *rdiag = d + k;
+    const double *SY = SYg, *YBY = YBYg;
+    long long ls = kmax;                                // row stride of SY / YBY
+    if (mats) {
+        double *S1 = rdiag + k, *S2 = S1 + (size_t)k * k;
+        for (int q = lane; q < k * k; q += 32) {
+            const int i = q / k, j = q - i * k;
+            S1[q] = __ldg(SYg + (long long)i * kmax + j);
+            S2[q] = __ldg(YBYg + (long long)i * kmax + j);
+        }
+        SY = S1;
+        YBY = S2;
+        ls = k;
+    }
+    for (int i = lane; i < k; i += 32) rdiag[i] = 1.0 / __ldg(SYg + (long long)i * kmax + i);
     __syncwarp();
-    double *cv = scratch + (long long)c * 2 * k, *d = cv + k;
     // R cv = T_top (back substitution), R_ij = s_i^T y_j upper
     for (int i = k - 1; i >= 0; --i) {
         double s = 0.0;
-        for (int j = i + 1 + lane; j < k; j += 32) s += __ldg(SY + (long long)i * kmax + j) * cv[j];
+        for (int j = i + 1 + lane; j < k; j += 32) s += SY[i * ls + j] * cv[j];
         s = warp_sum(s);
         if (lane == 0) cv[i] = (__ldg(T + (long long)i * p + c) - s) * rdiag[i];
         __syncwarp();
     }
     for (int i = 0; i < k; ++i) {
         double t = 0.0;
-        for (int j = lane; j < k; j += 32) t += __ldg(YBY + (long long)i * kmax + j) * cv[j];
+        for (int j = lane; j < k; j += 32) t += YBY[i * ls + j] * cv[j];
         t = warp_sum(t);
-        if (lane == 0)
-            d[i] = __ldg(SY + (long long)i * kmax + i) * cv[i] + gamma * t - gamma * __ldg(T + (long long)(k + i) * p + c);
+        if (lane == 0) d[i] = SY[i * ls + i] * cv[i] + gamma * t - gamma * __ldg(T + (long long)(k + i) * p + c);
     }
     __syncwarp();
     // R^T top = d (forward substitution); overwrite d with top
     for (int i = 0; i < k; ++i) {
         double s = 0.0;
-        for (int j = lane; j < i; j += 32) s += __ldg(SY + (long long)j * kmax + i) * d[j];
+        for (int j = lane; j < i; j += 32) s += SY[j * ls + i] * d[j];
         s = warp_sum(s);
         if (lane == 0) d[i] = (d[i] - s) * rdiag[i];
         __syncwarp();
@@ -322,27 +360,38 @@ __global__ void __launch_bounds__(32) small_gemm_kernel(int M, int N, int K, con
     if (outf) outf[(long long)i * ldo + j] = (float)acc;
 }
 
-// Block-cooperative cyclic Jacobi for a symmetric p x p matrix A (row-major,
-// overwritten by its eigenvalues on the diagonal); U accumulates the
-// eigenvectors as columns (must hold I on entry).  Round-robin pairing gives
-// P/2 disjoint rotations per round (P = p rounded up to even); the pairing
-// of every round is tabulated once; a round rotates every 2 x 2 block of A
-// (a pair of rows by a pair of columns) on both sides in one pass.  A pair is rotated only while
-// |a_pq| > rel_eps sqrt(|a_pp a_qq|) (the relative threshold of Demmel &
-// Veselic 1992, which also resolves small eigenvalues of a graded matrix)
-// and |a_pq| > abs_eps |A|_F (below that an entry is rounding noise of the
-// largest eigenvalues: rotating it changes nothing at this precision), with
-// (rel_eps, abs_eps) = (1e-15, 1e-16) in FP64 and (1e-7, 4e-7) in FP32; the
-// sweeps stop after one without a rotation, or after max_sweeps.
-// work: >= 2 P floats of rotations + P (P - 1) shorts of pairing (shared).
-template <typename T>
-__device__ void block_jacobi(T *A, T *U, int p, T *cs, short *pairs, int max_sweeps)
+// Block-cooperative cyclic Jacobi (FP32) for a symmetric p x p matrix A
+// (row-major, scaled to |A|_F = 1, overwritten by the rotated matrix, its
+// eigenvalues on the diagonal); U accumulates the eigenvectors as columns
+// (must hold I on entry).  Round-robin pairing gives P/2 disjoint rotations
+// per round (P = p rounded up to even); the pairing of every round is
+// tabulated once.  A pair is rotated only while |a_pq| > 1e-7 sqrt(|a_pp
+// a_qq|) (the relative threshold of Demmel & Veselic 1992, which also
+// resolves small eigenvalues of a graded matrix) and |a_pq| > 4e-7 |A|_F
+// (below that an entry is rounding noise of the largest eigenvalues:
+// rotating it changes nothing at this precision); the sweeps stop after one
+// without a rotation, or after max_sweeps.  The rotation annihilating
+// a_pq, with |theta| <= pi/4 and tan 2 theta = 2 a_pq / (a_qq - a_pp), comes
+// from the half-angle formulas: with d = a_qq - a_pp and rho = 1 / sqrt(d^2
+// + 4 a_pq^2), cos 2 theta = |d| rho, c = sqrt((1 + cos 2 theta) / 2) and
+// s = sign(d) a_pq rho / c: two reciprocal square roots and no division
+// (the scaling keeps d^2 + 4 a_pq^2 in range for every rotated pair).
+//
+// Work split without index divisions: every warp forms the round's
+// rotations itself in registers (lane l: the pairs l + 32 j, j < NJ; a
+// warp's row pair comes from its owner lane by a shuffle), a barrier, then
+// warp w rotates the 2 x 2 blocks (a pair of rows by a pair of columns, both
+// sides in one pass, in place; blocks of two unrotated pairs are skipped) of
+// the row pairs w, w + nwarps, .. against lane l's column pairs, and
+// U <- U J (element (i, pair m) belongs to lane m mod 32 of warp
+// i mod nwarps), a barrier.  P / 2 <= 32 NJ.  pairs: P (P - 1) shorts.
+template <int NJ>
+__device__ void block_jacobi(float *A, float *U, int p, short *pairs, int max_sweeps)
 {
     const int t = threadIdx.x, nt = blockDim.x;
-    constexpr T rel_eps = sizeof(T) == 8 ? (T)1e-15 : (T)1e-7;
-    constexpr T abs_eps = sizeof(T) == 8 ? (T)1e-16 : (T)4e-7;
+    const int lane = t & 31, warp = t >> 5, nw = nt >> 5;
+    const float rel2 = 1e-14f, abs_tol = 4e-7f;   // (1e-7)^2; 4e-7 |A|_F with |A|_F = 1
     __shared__ int rotated;
-    __shared__ T fro;
     const int P = (p + 1) & ~1;
     const int npair = P / 2;
     // pairs[round][m] = (a, b), a < b, round-robin with element 0 fixed
@@ -353,70 +402,84 @@ __device__ void block_jacobi(T *A, T *U, int p, T *cs, short *pairs, int max_swe
         pairs[2 * q] = (short)min(a, b);
         pairs[2 * q + 1] = (short)max(a, b);
     }
-    if (t == 0) fro = 0;
-    __syncthreads();
-    {
-        T f = 0;
-        for (int q = t; q < p * p; q += nt) f += A[q] * A[q];
-        atomicAdd(&fro, f);
-    }
-    __syncthreads();
-    const T abs_tol = abs_eps * sqrt(fro);
-    const int nblk = npair * npair;             // 2 x 2 blocks (pair of rows, pair of columns) of A
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (t == 0) rotated = 0;
         __syncthreads();
         for (int round = 0; round < P - 1; ++round) {
             const short *pr = pairs + 2 * round * npair;
-            for (int m = t; m < npair; m += nt) {
-                const int pp = pr[2 * m], qq = pr[2 * m + 1];
-                T c = 1, sn = 0;
-                if (qq < p) {
-                    const T apq = A[pp * p + qq];
-                    const T app = A[pp * p + pp], aqq = A[qq * p + qq];
-                    if (fabs(apq) > rel_eps * sqrt(fabs(app * aqq)) && fabs(apq) > abs_tol) {
-                        const T tau = (aqq - app) / (2 * apq);
-                        const T tt = (tau >= 0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
-                        c = (T)1 / sqrt((T)1 + tt * tt);
-                        sn = tt * c;
-                        rotated = 1;
+            float cr[NJ], sr[NJ];
+            int pm[NJ], qm[NJ];
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+                cr[j] = 1.f;
+                sr[j] = 0.f;
+                pm[j] = qm[j] = p;
+                const int m = lane + 32 * j;
+                if (m < npair) {
+                    const int pp = pr[2 * m], qq = pr[2 * m + 1];
+                    pm[j] = pp;
+                    qm[j] = qq;
+                    if (qq < p) {
+                        const float apq = A[pp * p + qq];
+                        const float app = A[pp * p + pp], aqq = A[qq * p + qq];
+                        if (apq * apq > rel2 * fabsf(app * aqq) && fabsf(apq) > abs_tol) {
+                            const float d = aqq - app, two = 2.f * apq;
+                            const float rho = rsqrtf(fmaf(d, d, two * two));
+                            const float x = fmaf(0.5f * fabsf(d), rho, 0.5f);      // c^2
+                            const float rx = rsqrtf(x);                            // 1 / c
+                            cr[j] = x * rx;
+                            sr[j] = copysignf(1.f, d) * (apq * rho) * rx;
+                            any = true;
+                        }
                     }
                 }
-                cs[2 * m] = c;
-                cs[2 * m + 1] = sn;
             }
-            __syncthreads();
-            // A <- J^T A J in one pass: every 2 x 2 block (rows of pair m1,
-            // columns of pair m2) is read once, rotated on both sides, written
-            // once; U <- U J on the same pass
-            for (int q = t; q < nblk; q += nt) {
-                const int m1 = q / npair, m2 = q - m1 * npair;
-                const T s1 = cs[2 * m1 + 1], s2 = cs[2 * m2 + 1];
-                if (s1 == 0 && s2 == 0) continue;
-                const T c1 = cs[2 * m1], c2 = cs[2 * m2];
-                const int p1 = pr[2 * m1], q1 = pr[2 * m1 + 1], p2 = pr[2 * m2], q2 = pr[2 * m2 + 1];
-                const bool hq1 = q1 < p, hq2 = q2 < p;
-                const T a = A[p1 * p + p2];
-                const T b = hq2 ? A[p1 * p + q2] : (T)0;
-                const T cc = hq1 ? A[q1 * p + p2] : (T)0;
-                const T d = (hq1 && hq2) ? A[q1 * p + q2] : (T)0;
-                // rows (pair m1), then columns (pair m2)
-                const T ra = c1 * a - s1 * cc, rc = s1 * a + c1 * cc;
-                const T rb = c1 * b - s1 * d, rd = s1 * b + c1 * d;
-                A[p1 * p + p2] = c2 * ra - s2 * rb;
-                if (hq2) A[p1 * p + q2] = s2 * ra + c2 * rb;
-                if (hq1) A[q1 * p + p2] = c2 * rc - s2 * rd;
-                if (hq1 && hq2) A[q1 * p + q2] = s2 * rc + c2 * rd;
+            if (warp == 0 && any) rotated = 1;
+            __syncthreads();                    // every rotation read its pair before any update
+            for (int m1 = warp; m1 < npair; m1 += nw) {
+                const int o = m1 & 31, j1 = m1 >> 5;
+                float c1 = cr[0], s1 = sr[0];
+                int p1 = pm[0], q1 = qm[0];
+#pragma unroll
+                for (int j = 1; j < NJ; ++j)
+                    if (j == j1) { c1 = cr[j]; s1 = sr[j]; p1 = pm[j]; q1 = qm[j]; }
+                c1 = __shfl_sync(0xffffffffu, c1, o);
+                s1 = __shfl_sync(0xffffffffu, s1, o);
+                p1 = __shfl_sync(0xffffffffu, p1, o);
+                q1 = __shfl_sync(0xffffffffu, q1, o);
+                const bool hq1 = q1 < p;
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) {
+                    const float c2 = cr[j], s2 = sr[j];
+                    if (lane + 32 * j >= npair || (s1 == 0.f && s2 == 0.f)) continue;
+                    const int p2 = pm[j], q2 = qm[j];
+                    const bool hq2 = q2 < p;
+                    float *r1 = A + p1 * p, *r2 = A + q1 * p;
+                    const float a = r1[p2];
+                    const float b = hq2 ? r1[q2] : 0.f;
+                    const float cc = hq1 ? r2[p2] : 0.f;
+                    const float d = (hq1 && hq2) ? r2[q2] : 0.f;
+                    // rows (pair m1), then columns (pair m2)
+                    const float ra = c1 * a - s1 * cc, rc = s1 * a + c1 * cc;
+                    const float rb = c1 * b - s1 * d, rd = s1 * b + c1 * d;
+                    r1[p2] = c2 * ra - s2 * rb;
+                    if (hq2) r1[q2] = s2 * ra + c2 * rb;
+                    if (hq1) r2[p2] = c2 * rc - s2 * rd;
+                    if (hq1 && hq2) r2[q2] = s2 * rc + c2 * rd;
+                }
             }
-            for (int q = t; q < p * npair; q += nt) {
-                const int l = q / npair, m = q - l * npair;
-                const T sn = cs[2 * m + 1];
-                if (sn == 0) continue;
-                const int pp = pr[2 * m], qq = pr[2 * m + 1];
-                const T c = cs[2 * m];
-                const T u = U[l * p + pp], v = U[l * p + qq];
-                U[l * p + pp] = c * u - sn * v;
-                U[l * p + qq] = sn * u + c * v;
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+                if (sr[j] == 0.f) continue;
+                const int pp = pm[j], qq = qm[j];
+                const float c = cr[j], sn = sr[j];
+                for (int l = warp; l < p; l += nw) {
+                    float *ur = U + l * p;
+                    const float u = ur[pp], v = ur[qq];
+                    ur[pp] = c * u - sn * v;
+                    ur[qq] = sn * u + c * v;
+                }
             }
             __syncthreads();
         }
@@ -454,6 +517,32 @@ __global__ void __launch_bounds__(512) gram_pivchol_kernel(const double *__restr
     double *rinv = Ri + pp + p;                         // 1 / R_jj
     __shared__ int s_r, s_go;
     __shared__ double s_dinv, s_d0;
+    if (tol == 0.0) {
+        // CholeskyQR pass: a block already orthonormal to 1e-9 (far below
+        // FP32 rounding) keeps its basis, coef = I
+        __shared__ double s_dev[16];
+        // largest deviation from I; a NaN sticks (it then fails the test
+        // below, and the factorisation flags it)
+        auto dmax = [](double a, double b) { return (b > a || b != b) ? b : a; };
+        double dev = 0.0;
+        for (long long q = t; q < pp; q += nt) {
+            const long long i = q / p;
+            dev = dmax(dev, fabs(G[q] - (q == i * p + i ? 1.0 : 0.0)));
+        }
+        for (int o = 16; o > 0; o >>= 1) dev = dmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+        if (tx == 0) s_dev[ty] = dev;
+        __syncthreads();
+        dev = 0.0;
+        for (int w = 0; w < (nt >> 5); ++w) dev = dmax(dev, s_dev[w]);
+        if (dev <= 1e-9) {
+            for (long long q = t; q < pp; q += nt) {
+                const long long i = q / p;
+                coef[q] = q == i * p + i ? 1.0 : 0.0;
+            }
+            if (t == 0) *r_out = p;
+            return;
+        }
+    }
     for (long long q = t; q < pp; q += nt) {
         A[q] = G[q];
         R[q] = 0.0;
@@ -465,19 +554,13 @@ __global__ void __launch_bounds__(512) gram_pivchol_kernel(const double *__restr
         if (t < 32) {
             // largest remaining residual (first index among equals), warp 0
             int best = -1;
-            double bv = -1.0;
+            double bv = 0.0;
             for (int k = j + t; k < p; k += 32) {
                 const double d = A[(long long)piv[k] * p + piv[k]];
-                if (d > bv) { bv = d; best = k; }
+                if (best < 0 || __double_as_longlong(d) > __double_as_longlong(bv)) { bv = d; best = k; }
             }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const double ov = __shfl_down_sync(0xffffffffu, bv, off);
-                const int ob = __shfl_down_sync(0xffffffffu, best, off);
-                if (ov > bv || (ov == bv && ob >= 0 && (best < 0 || ob < best))) { bv = ov; best = ob; }
-            }
-            bv = __shfl_sync(0xffffffffu, bv, 0);
-            best = __shfl_sync(0xffffffffu, best, 0);
+            warp_argmax_nonneg(bv, best);
+            if (best < 0) bv = -1.0;
             if (t == 0 && j == 0) {
                 s_d0 = bv;
                 if (!(bv > 0.0) || !isfinite(bv)) *flag = 1;
@@ -509,16 +592,18 @@ __global__ void __launch_bounds__(512) gram_pivchol_kernel(const double *__restr
         }
         __syncthreads();
         if (!s_go) break;
-        // row j of R and the trailing update in one pass (neither touches
-        // row or column piv[j] of A, which both read)
+        // row j of R, then the trailing update from it (one FP64 FMA per
+        // element; neither touches row or column piv[j] of A)
         const int pj = piv[j];
         const double dinv = s_dinv;
         const double *Aj = A + (long long)pj * p;
-        for (int k = j + 1 + t; k < p; k += nt) R[(long long)j * p + k] = Aj[piv[k]] * dinv;
+        double *Rj = R + (long long)j * p;
+        for (int k = j + 1 + t; k < p; k += nt) Rj[k] = Aj[piv[k]] * dinv;
+        __syncthreads();
         for (int kk = j + 1 + ty; kk < p; kk += 16) {
-            const int pk = piv[kk];
-            const double rk = Aj[pk] * dinv;
-            for (int ll = j + 1 + tx; ll < p; ll += 32) A[(long long)pk * p + piv[ll]] -= rk * (Aj[piv[ll]] * dinv);
+            const double rk = Rj[kk];
+            double *Ak = A + (long long)piv[kk] * p;
+            for (int ll = j + 1 + tx; ll < p; ll += 32) Ak[piv[ll]] = fma(-rk, Rj[ll], Ak[piv[ll]]);
         }
         __syncthreads();
     }
@@ -558,9 +643,10 @@ __global__ void __launch_bounds__(512) gram_pivchol_kernel(const double *__restr
 // Eigenpairs of the Jacobi result (eigenvalues on the diagonal of Af,
 // eigenvectors in the columns of Uf, r x r) ordered by |lambda| descending
 // (the first index among equal magnitudes): lam[k] and coef [rank][r] = U^T,
-// zero beyond r.  Each eigenvalue's position is its count of larger ones, so
-// every thread places its own.  A non-finite eigenvalue sets flag 4.
-__device__ void select_eigenpairs(const float *Af, const float *Uf, int r, int rank, double *__restrict__ lam,
+// zero beyond r; the eigenvalues are the diagonal times scale.  Each
+// eigenvalue's position is its count of larger ones, so every thread places
+// its own.  A non-finite eigenvalue sets flag 4.
+__device__ void select_eigenpairs(const float *Af, const float *Uf, int r, int rank, double scale, double *__restrict__ lam,
                                   float *__restrict__ coef, int *__restrict__ flag)
 {
     const int t = threadIdx.x, nt = blockDim.x;
@@ -573,7 +659,7 @@ __device__ void select_eigenpairs(const float *Af, const float *Uf, int r, int r
             pos += (vj > vi || (vj == vi && j < i)) ? 1 : 0;
         }
         if (pos < rank) {
-            lam[pos] = (double)Af[(long long)i * r + i];
+            lam[pos] = (double)Af[(long long)i * r + i] * scale;
             for (int a = 0; a < r; ++a) coef[(long long)pos * r + a] = Uf[(long long)a * r + i];
         }
     }
@@ -639,19 +725,13 @@ __global__ void __launch_bounds__(512) lu_kernel(double *__restrict__ M, double 
     for (int j = 0; j < r; ++j) {
         if (threadIdx.x < 32) {
             int best = -1;
-            double bv = -1.0;
+            double bv = 0.0;
             for (int a = j + tx; a < r; a += 32) {
                 const double v = fabs(A[a * r + j]);
-                if (v > bv) { bv = v; best = a; }
+                if (best < 0 || __double_as_longlong(v) > __double_as_longlong(bv)) { bv = v; best = a; }
             }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const double ov = __shfl_down_sync(0xffffffffu, bv, off);
-                const int ob = __shfl_down_sync(0xffffffffu, best, off);
-                if (ov > bv || (ov == bv && ob >= 0 && (best < 0 || ob < best))) { bv = ov; best = ob; }
-            }
-            best = __shfl_sync(0xffffffffu, best, 0);
-            bv = __shfl_sync(0xffffffffu, bv, 0);
+            warp_argmax_nonneg(bv, best);
+            if (best < 0) bv = -1.0;
             if (best < 0) best = j;
             if (tx == 0) {
                 if (!(bv > 0.0)) *flag = 3;
@@ -694,10 +774,14 @@ __global__ void __launch_bounds__(32) lu_solve_kernel(const double *__restrict__
                                                       const int *__restrict__ perm, const double *__restrict__ Bt,
                                                       int r, double *__restrict__ X, int use_smem)
 {
-    __shared__ double x[256];
+    __shared__ double x[256], rd[256];
     extern __shared__ double lus_smem[];
     const int c = blockIdx.x, lane = threadIdx.x;
     if (c >= r) return;
+    for (int i = lane; i < r; i += 32) {                 // reciprocal pivots, off the solve's chain
+        const double d = U[(long long)i * r + i];
+        rd[i] = d == 0.0 ? 1.0 : 1.0 / d;
+    }
     if (use_smem) {
         double *Us = lus_smem, *Lsm = lus_smem + (size_t)r * r;
         for (int q = lane; q < r * r; q += 32) {
@@ -731,11 +815,7 @@ __global__ void __launch_bounds__(32) lu_solve_kernel(const double *__restrict__
         double sacc = 0.0;
         for (int j = i + 1 + lane; j < r; j += 32) sacc += U[(long long)i * r + j] * x[j];
         sacc = warp_sum(sacc);
-        if (lane == 0) {
-            double d = U[(long long)i * r + i];
-            if (d == 0.0) d = 1.0;
-            x[i] = (x[i] - sacc) / d;
-        }
+        if (lane == 0) x[i] = (x[i] - sacc) * rd[i];
         __syncwarp();
     }
     for (int i = lane; i < r; i += 32) X[(long long)i * r + c] = x[i];
@@ -771,24 +851,39 @@ __global__ void sym_kernel(double *__restrict__ T, int r)
 
 // Eigenpairs of a symmetric r x r matrix T (FP32 block Jacobi), ordered by
 // |lambda| descending: lam[rank] and coef [rank][r] = U^T (zero rows
-// beyond r).  work: >= r^2 + r + 16 + (r + 2)^2 / 4 doubles (or shared memory).
-__global__ void eig_select_kernel(const double *__restrict__ T, int r, int rank, double *work,
-                                  double *__restrict__ lam, float *__restrict__ coef, int *__restrict__ flag,
-                                  int use_smem)
+// beyond r).  r <= 32 * 2 NJ.  work: >= eig_work_doubles(r) doubles (or shared memory).
+__host__ __device__ inline size_t eig_work_doubles(int r)
+{
+    return (size_t)r * r + ((size_t)r + 2) * (r + 2) / 4 + 16;
+}
+
+template <int NJ>
+__global__ void __launch_bounds__(1024, 1) eig_select_kernel(const double *__restrict__ T, int r, int rank, double *work,
+                                                          double *__restrict__ lam, float *__restrict__ coef,
+                                                          int *__restrict__ flag, int use_smem)
 {
     extern __shared__ double smem_work[];
     if (use_smem) work = smem_work;
     const int t = threadIdx.x, nt = blockDim.x;
-    float *Af = reinterpret_cast<float *>(work);
-    float *Uf = Af + (long long)r * r;
-    float *csf = Uf + (long long)r * r;            // >= r + 2 floats
-    short *pairs = reinterpret_cast<short *>(csf + r + 2);   // (r + 1)^2 shorts
+    float *A0 = reinterpret_cast<float *>(work);
+    float *Uf = A0 + (long long)r * r;
+    short *pairs = reinterpret_cast<short *>(Uf + (long long)r * r);   // (r + 1)^2 shorts
+    // |T|_F in FP64 (a non-finite T gives non-finite eigenvalues: flag 4)
+    __shared__ double s_f[32];
+    double f = 0.0;
+    for (int q = t; q < r * r; q += nt) f += T[q] * T[q];
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if ((t & 31) == 0) s_f[t >> 5] = f;
+    __syncthreads();
+    f = 0.0;
+    for (int w = 0; w < (nt >> 5); ++w) f += s_f[w];
+    const double fro = sqrt(f), sc = fro > 0.0 ? 1.0 / fro : 1.0;
     for (int q = t; q < r * r; q += nt) {
-        Af[q] = (float)T[q];
+        A0[q] = (float)(T[q] * sc);
         Uf[q] = (q / r == q % r) ? 1.f : 0.f;
     }
-    block_jacobi<float>(Af, Uf, r, csf, pairs, 40);
-    select_eigenpairs(Af, Uf, r, rank, lam, coef, flag);
+    block_jacobi<NJ>(A0, Uf, r, pairs, 40);
+    select_eigenpairs(A0, Uf, r, rank, fro > 0.0 ? fro : 1.0, lam, coef, flag);
 }
 
 __global__ void std_kernel(const float *__restrict__ V, long long ldv, const double *__restrict__ lam, int rank,
@@ -961,8 +1056,22 @@ int unstage_rows(gbfwi_bfgs *h, float *user, const float *dev, int rows, cudaStr
     return GBFWI_OK;
 }
 
-// FP64 scratch of apply_dev (T and per-column vectors), placed first in `small`
-size_t small_apply_doubles(const gbfwi_bfgs *h, int p) { return (size_t)4 * std::max(h->k, 1) * p + 64; }
+// FP64 scratch of apply_dev (T = [S; B0 Y] X^T), placed first in `small`
+size_t small_apply_doubles(const gbfwi_bfgs *h, int p) { return (size_t)2 * std::max(h->k, 1) * p + 64; }
+
+// coef / coefd [q][2k] = (M T)^T for the q columns of T [2k][q] (middle_kernel)
+int launch_middle(gbfwi_bfgs *h, const double *T, int q, double gamma, float *coef, double *coefd, cudaStream_t s)
+{
+    const int k = h->k;
+    const int mats = middle_smem_bytes(k, true) <= 200 * 1024;
+    const size_t bytes = middle_smem_bytes(k, mats);
+    if (bytes > 48 * 1024)
+        GB_CUDA(cudaFuncSetAttribute(middle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    middle_kernel<<<q, 32, bytes, s>>>(T, h->dSY.as<double>(), h->dYBY.as<double>(), k, h->kmax, q, gamma, mats,
+                                       coef, coefd);
+    GB_LAUNCHED();
+    return GBFWI_OK;
+}
 
 // Size the scratch buffers once per call so that nothing is reallocated
 // while kernels queued earlier in the same call may still use it.
@@ -996,7 +1105,6 @@ int apply_dev(gbfwi_bfgs *h, const float *Xd, long long ldx, int p, float *Zd, l
         return combine(h, nullptr, nullptr, 0, 0, nullptr, p, Zd, ldz, h->B0.as<float>(), Xd, ldx, beta, s);
     }
     double *T = h->small.as<double>();
-    double *scr = T + 2 * k * p;
     // T = [S; B0 Y] X^T: rows 0..k-1 S^T x_c, rows k..2k-1 (B0 Y)^T x_c, one pass over X
     if (p <= 2 && ldx != h->ld) {
         // a caller's one or two vectors with their own pitch: thin products
@@ -1019,9 +1127,7 @@ int apply_dev(gbfwi_bfgs *h, const float *Xd, long long ldx, int p, float *Zd, l
     } else {
         GB_TRY(atb(h, h->S.as<float>(), h->BY.as<float>(), k, 2 * k, Xd, nullptr, p, p, T, p, s));
     }
-    middle_kernel<<<p, 32, (size_t)k * sizeof(double), s>>>(T, h->dSY.as<double>(), h->dYBY.as<double>(), k,
-                                                            h->kmax, p, gamma, scr, h->coef.as<float>(), nullptr);
-    GB_LAUNCHED();
+    GB_TRY(launch_middle(h, T, p, gamma, h->coef.as<float>(), nullptr, s));
     return combine(h, h->S.as<float>(), h->BY.as<float>(), k, 2 * k, h->coef.as<float>(), p, Zd, ldz,
                    h->B0.as<float>(), Xd, ldx, beta, s);
 }
@@ -1230,11 +1336,12 @@ int launch_pivchol(const double *G, int p, double tol, double *work, double *coe
 
 int launch_eig(const double *T, int r, int rank, double *work, double *lam, float *coef, int *flag, cudaStream_t s)
 {
-    const size_t we = ((size_t)r * r + r + 16 + ((size_t)r + 2) * (r + 2) / 4) * sizeof(double);
+    const size_t we = eig_work_doubles(r) * sizeof(double);
     const int use_smem = we <= 200 * 1024;
-    if (use_smem)
-        GB_CUDA(cudaFuncSetAttribute(eig_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)we));
-    eig_select_kernel<<<1, 512, use_smem ? we : 0, s>>>(T, r, rank, work, lam, coef, flag, use_smem);
+    const int npair = (r + 1) / 2;
+    auto kern = npair <= 32 ? eig_select_kernel<1> : npair <= 64 ? eig_select_kernel<2> : eig_select_kernel<4>;
+    if (use_smem) GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)we));
+    kern<<<1, 1024, use_smem ? we : 0, s>>>(T, r, rank, work, lam, coef, flag, use_smem);
     GB_LAUNCHED();
     return GBFWI_OK;
 }
@@ -1291,13 +1398,10 @@ int basis_coords(gbfwi_bfgs *h, const double *Gb, const double *Cb, int q, int m
 // Y = G Tq^T ([m][r]), symmetrised into Cm [r][r]
 int rayleigh_ritz(gbfwi_bfgs *h, const double *Tq, int r, int m, Arena &ar, double *Cm, cudaStream_t s)
 {
-    const int k = h->k;
     const double *G = h->dG.as<double>();
-    double *Yc = ar.take((size_t)m * r), *CdY = ar.take((size_t)r * m), *mid = ar.take((size_t)r * m);
+    double *Yc = ar.take((size_t)m * r), *CdY = ar.take((size_t)r * m);
     GB_TRY(gemm(m, r, m, G, m, 1, Tq, 1, m, Yc, nullptr, r, s));               // Y = G Tq^T
-    middle_kernel<<<r, 32, (size_t)k * sizeof(double), s>>>(Yc, h->dSY.as<double>(), h->dYBY.as<double>(), k,
-                                                            h->kmax, r, 1.0, mid, nullptr, CdY);   // (M Y)^T
-    GB_LAUNCHED();
+    GB_TRY(launch_middle(h, Yc, r, 1.0, nullptr, CdY, s));                      // (M Y)^T
     GB_TRY(gemm(r, r, m, CdY, m, 1, Yc, r, 1, Cm, nullptr, r, s));             // Y^T M Y
     sym_kernel<<<1, 256, 0, s>>>(Cm, r);
     GB_LAUNCHED();
@@ -1370,7 +1474,7 @@ int lowrank_randomized(gbfwi_bfgs *h, const float *X, int p, int rank, unsigned 
     GB_TRY(h->ex.ensure(lowrank_doubles(p, m) * sizeof(double)));
     Arena ar{h->ex.as<double>()};
     const size_t pm = (size_t)p * m, pp = (size_t)p * p;
-    double *Z = ar.take(pm), *Cd = ar.take(pm), *Pm = ar.take(pm), *mid = ar.take(pm), *Ge = ar.take(pp);
+    double *Z = ar.take(pm), *Cd = ar.take(pm), *Pm = ar.take(pm), *Ge = ar.take(pp);
     double *lam = ar.take((size_t)p + 2);
     int *rdev = reinterpret_cast<int *>(ar.take(2));
     int *flag = h->flag.as<int>();
@@ -1378,9 +1482,7 @@ int lowrank_randomized(gbfwi_bfgs *h, const float *X, int p, int rank, unsigned 
     GB_CUDA(cudaMemsetAsync(flag, 0, 16, s));
     // 1. Z = W^T X (one pass over S, B0 Y and X), C = (M Z)^T: E = C W
     GB_TRY(atb(h, h->S.as<float>(), h->BY.as<float>(), k, m, Xd, nullptr, p, p, Z, p, s));
-    middle_kernel<<<p, 32, (size_t)k * sizeof(double), s>>>(Z, h->dSY.as<double>(), h->dYBY.as<double>(), k, h->kmax,
-                                                            p, 1.0, mid, nullptr, Cd);
-    GB_LAUNCHED();
+    GB_TRY(launch_middle(h, Z, p, 1.0, nullptr, Cd, s));
     // 2. E E^T = C G C^T, the basis coordinates Tq
     GB_TRY(gemm(p, m, m, Cd, m, 1, G, m, 1, Pm, nullptr, m, s));               // P = C G
     GB_TRY(gemm(p, p, m, Pm, m, 1, Cd, 1, m, Ge, nullptr, p, s));              // E E^T = P C^T
