@@ -46,7 +46,7 @@ import synth  # noqa: E402
 METRIC = "GLL-point-updates/s fwd+adj+kernel (HBM % peak); s per FWI gradient; s per rank-k UQ"
 ADJ_BYTES_PER_POINT = 76       # adjoint step: w r/w 16, wh r/w 16, material 12, u_k 8, 3 accumulators r/w 24
 FWD_BYTES_PER_POINT = 44       # forward step: u r/w 16, vh r/w 16, material 12
-UQ_ALG_ROWS = 620              # FP32 rows of n one rank-k UQ must move at least (S, B0 Y twice, X twice, E, basis, V)
+UQ_ALG_ROWS = 372              # FP32 rows of n one rank-k UQ moves: S, B0 Y twice (200), X written and read (120), V (50), B0 and std (2)
 
 
 def parse():
@@ -511,8 +511,10 @@ def run_ours(args):
     roof_uq = {"bound": "hbm", "achieved": uq_bytes / (uq_ms / 1e3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
                "frac": uq_bytes / (uq_ms / 1e3) / 1e9 / pk["hbm_gbs"], "algorithmic_bytes": uq_bytes,
                "s_per_uq": uq_ms / 1e3, "peak_kind": pk_kind,
-               "definition": f"{UQ_ALG_ROWS} FP32 rows of n: two passes over S and B0 Y (200), X read twice "
-                             "and E written (180), the basis and V passes (4 x 60)",
+               "definition": f"{UQ_ALG_ROWS} FP32 rows of n: the probes X written and read once (2 x 60), "
+                             "S and B0 Y read by W^T X and by V = (U^T T) W (2 x 100), V written (50), B0 read "
+                             "and the std written (2); every other block of the decomposition lives in the "
+                             "coordinates of W (small FP64 matrices)",
                "timing": "CUDA events around gbfwi_lowrank_invhess"}
 
     c3 = None

@@ -218,10 +218,12 @@ int gbfwi_bfgs_apply(gbfwi_bfgs *b, const float *X, int p, float *Z, double gamm
  * (may be NULL), lambda: [rank] FP64 (may be NULL), std: [n] (may be NULL).
  * Q is rank-revealing: pivoted Cholesky of the FP64 Gram matrix E E^T (QR
  * with column pivoting on E) keeps the probe rows whose residual norm is at
- * least 1e-4 of the largest (an FP32 block resolves nothing finer), so
+ * least 1e-4 of the largest (the FP32 data resolve nothing finer), so
  * r = dim Q <= p; Omega (r x r) is then the least-squares solution, equal to
  * the solve above when r = p, and eigenpairs beyond r are returned as
- * lambda = 0 with zero rows of V.
+ * lambda = 0 with zero rows of V.  E, Q and the projections are formed in
+ * the coordinates of W = [S, B0 Y] (E = C W with C = (M W^T X)^T, the store
+ * keeps W^T W), so the n-long work is W^T X and V only.
  * 1 <= rank <= p <= 256.  Synchronises the stream.
  * -> EINVAL, ECUDA, ENOMEM, ENONFINITE (E = 0 or non-finite, a singular
  *    Q^T X). */
@@ -235,7 +237,8 @@ int gbfwi_lowrank_invhess(gbfwi_bfgs *b, const float *X, int p, int rank,
  * a second application of the compact form to the basis,
  * C = Q (B_{n+1} - B0) Q^T (r x r, symmetrised), U Lambda U^T = C,
  * V = U^T Q.  It avoids the (Q^T X)^-1 of the single pass, whose error
- * grows with cond(Q^T X), for the cost of one more block apply (r rows).
+ * grows with cond(Q^T X); in the coordinates of W the second application
+ * is a product of small matrices, (G T^T)^T M (G T^T), with G = W^T W.
  * Arguments, outputs and errors as gbfwi_lowrank_invhess.  Synchronises
  * the stream. */
 int gbfwi_lowrank_twopass(gbfwi_bfgs *b, const float *X, int p, int rank,
@@ -246,9 +249,10 @@ int gbfwi_lowrank_twopass(gbfwi_bfgs *b, const float *X, int p, int rank,
  * random probes).  In compact form B_{n+1} - B0 = W M W^T with W = [S, B0 Y]
  * (n x 2k) and M = [[R^-T (D + Y^T B0 Y) R^-1, -R^-T], [-R^-1, 0]], so its
  * rank is at most 2k: Q (orthonormal rows spanning the rows of W^T) from
- * pivoted Cholesky of the column-scaled FP64 Gram matrix W^T W (QR with
- * column pivoting; directions below 1e-4 of the largest dropped) and shifted
- * CholeskyQR3, then U Lambda U^T = (Q W) M (Q W)^T and V = U^T Q.
+ * pivoted Cholesky of the column-scaled FP64 Gram matrix W^T W kept by the
+ * store (QR with column pivoting; directions below 1e-4 of the largest
+ * dropped) and one CholeskyQR pass, both on coordinates (Q = T W^T), then
+ * U Lambda U^T = (Q W) M (Q W)^T and V = U^T Q (the one n-long pass).
  * Eigenpairs ordered by |lambda| descending; std as in
  * gbfwi_lowrank_invhess.  V: [rank][n] (may be NULL), lambda: [rank] FP64
  * (may be NULL), std: [n] (may be NULL).  1 <= k <= 128 stored pairs,

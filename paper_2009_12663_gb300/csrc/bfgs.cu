@@ -9,21 +9,24 @@
 // with R_ij = s_i^T y_j (i <= j), D = diag(s_i^T y_i).  It equals the
 // recursion of Eq. 3 and the two-loop recursions of Algorithms 1-2.
 //
-// Layout: vectors are rows, S / Y / B0Y are [kmax][ld] FP32, blocks X / E / Q /
-// V are [p][ld] FP32, with the row pitch ld = n rounded up to 64 floats so
+// Layout: vectors are rows, S / Y / B0Y are [kmax][ld] FP32, blocks X / V
+// are [p][ld] FP32, with the row pitch ld = n rounded up to 64 floats so
 // that every row starts on a 256-byte boundary.  The n-long work is (a)
-// split-K products A B^T on the tensor cores (3xTF32, compensated sums
+// split-K products A B^T on the tcgen05 tensor cores (exact three-part
+// bfloat16 split, a fresh accumulator per 16-deep step, compensated sums
 // within a split, a deterministic FP64 reduction over the splits;
-// tc_products.cu), or compensated CUDA-core dot products for one or two
+// tc_products.cu), or compensated CUDA-core dot products for up to three
 // columns, and (b) row combinations out = coef * rows on the tensor cores;
-// the small matrices (middle matrix, pivoted and plain Cholesky factors,
-// the solve for Omega) are FP64 in one CTA, and the small symmetric
-// eigenproblems run as FP32 block Jacobi sweeps in one CTA.
+// the small matrices are FP64 (products spread over SMs, factorisations and
+// solves in one CTA or one warp per right-hand side), and the small
+// symmetric eigenproblems run as FP32 block Jacobi sweeps in one CTA.
 //
 // The low-rank part (Algorithm 3, gbfwi_lowrank_invhess): E = (B - B0) X,
-// a rank-revealing orthonormal basis Q of E (pivoted Cholesky of E E^T,
-// shifted CholeskyQR3), Omega (Q X) = Q E by least squares, Omega = U L U^T,
-// V = U^T Q.  gbfwi_lowrank_exact takes Q from [S, B0 Y] instead of probes.
+// a rank-revealing orthonormal basis Q of E (pivoted Cholesky of E E^T and
+// one CholeskyQR pass), Omega (Q X) = Q E by least squares, Omega = U L U^T,
+// V = U^T Q, all carried out in the coordinates of W = [S, B0 Y] with the
+// Gram matrix W^T W kept by the update (see basis_coords).
+// gbfwi_lowrank_exact takes Q from W itself instead of probes.
 
 #include <algorithm>
 #include <cmath>
@@ -985,7 +988,7 @@ size_t part_need(const gbfwi_bfgs *h, int ka, int kb)
 // out[a][b] = sum_i A_a[i] B_b[i] -> out (device FP64, row stride ldo); the
 // A rows a < ka1 come from A1, the rest from A2 (likewise B).  Rows have the
 // store's pitch.  One or two columns from a single B block: compensated
-// CUDA-core dot products; otherwise the tensor-core 3xTF32 product.
+// CUDA-core dot products; otherwise the tcgen05 product (gb_tc_atb).
 int atb(gbfwi_bfgs *h, const float *A1, const float *A2, int ka1, int ka, const float *B1, const float *B2, int kb1,
         int kb, double *out, long long ldo, cudaStream_t s)
 {
