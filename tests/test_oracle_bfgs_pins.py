@@ -161,3 +161,29 @@ def test_two_pass_rsvd_on_bfgs_history_equals_dense_eigh():
     assert np.allclose(l, le, rtol=1e-8, atol=1e-12 * np.abs(le).max())
     for j in range(2 * k):
         assert abs(abs(V[j] @ Ve[j]) - 1) < 1e-7
+
+
+def test_probe_block_lies_in_span_of_pairs_with_compact_coordinates():
+    """The compact representation of Byrd, Nocedal & Schnabel (1994):
+    B_{n+1} - B0 = W M W^T with W = [S, B0 Y] (rows s_i, B0 y_i) and
+    M = [[R^-T (D + Y^T B0 Y) R^-1, -R^-T], [-R^-1, 0]], R_ij = s_i^T y_j
+    (i <= j), D = diag(s_i^T y_i).  So every row of E = (B_{n+1} - B0) X of
+    Algorithm 2 lies in the span of the pairs, with coordinates
+    C = (M W^T X)^T.  A two-loop recursion that kept the B0 e term, or put
+    B0 on the wrong side of a loop, leaves E outside that span."""
+    S, Y, B0 = _pairs(80, 7)
+    k = len(S)
+    X = RNG.standard_normal((9, 80))
+    E = bfgs.probe_block(X, S, Y, B0)
+    W = np.vstack([S, B0 * Y])
+    Qw, _ = np.linalg.qr(W.T)
+    outside = E - (E @ Qw) @ Qw.T
+    assert np.abs(outside).max() < 1e-12 * np.abs(E).max()
+    SY = S @ Y.T
+    R = np.triu(SY)
+    D = np.diag(np.diag(SY))
+    YBY = Y @ (B0 * Y).T
+    Ri = np.linalg.inv(R)
+    M = np.block([[Ri.T @ (D + YBY) @ Ri, -Ri.T], [-Ri, np.zeros((k, k))]])
+    C = (M @ (W @ X.T)).T
+    assert np.abs(C @ W - E).max() < 1e-12 * np.abs(E).max()
