@@ -127,8 +127,11 @@ def run(iterations=15, sigma=100.0, rank=None, workload="small", variants=None, 
     Ve = torch.zeros(2 * k, n, device=true.device)
     store.lowrank_exact(2 * k, eps_prior=1.0, V=Ve, lam=le)
     spectra["exact_rank_2k"] = le.cpu().numpy().tolist()
-    Vh = Ve.double()
-    spectra["exact_V_orthonormality_max_error"] = float((Vh @ Vh.T - torch.eye(2 * k, device=Vh.device,
+    # resolved directions only: the rows beyond the basis rank are returned as zero
+    nres = int((le != 0).sum())
+    Vh = Ve[:nres].double()
+    spectra["exact_resolved_directions"] = nres
+    spectra["exact_V_orthonormality_max_error"] = float((Vh @ Vh.T - torch.eye(nres, device=Vh.device,
                                                                               dtype=Vh.dtype)).abs().max())
     out["uq_P4"] = {"pairs": k, "probes": p, "rank": r, "eigenvalues": lam.cpu().numpy().tolist(),
                     "spectra": spectra,
