@@ -341,6 +341,111 @@ __global__ void __launch_bounds__(32) middle_kernel(const double *__restrict__ T
     }
 }
 
+// The same product with the solves column-oriented, for k <= 32 NJ: lane l
+// owns the unknowns l + 32 t (t < NJ) in registers; step i of a triangular
+// solve is one multiply by the precomputed reciprocal pivot on the owner
+// lane, a shuffle of the result and one FMA per owned unknown, so the
+// dependent chain per step is three FP64 operations instead of a warp
+// reduction (five dependent FP64 adds).  Y^T B0 Y cv accumulates the same
+// way over the broadcast cv_i.  Shared memory and outputs as middle_kernel.
+template <int NJ>
+__device__ __forceinline__ double pick_nj(const double (&v)[NJ], int t)
+{
+    double r = v[0];
+#pragma unroll
+    for (int q = 1; q < NJ; ++q)
+        if (q == t) r = v[q];
+    return r;
+}
+
+template <int NJ>
+__global__ void __launch_bounds__(32) middle_col_kernel(const double *__restrict__ T, const double *__restrict__ SYg,
+                                                        const double *__restrict__ YBYg, int k, int kmax, int p,
+                                                        double gamma, int mats, float *__restrict__ coef,
+                                                        double *__restrict__ coefd)
+{
+    extern __shared__ double msm[];
+    const int c = blockIdx.x, lane = threadIdx.x;
+    if (c >= p) return;
+    double *rdiag = msm + 2 * k;                        // the layout of middle_kernel: cv, d, rdiag, R, YBY
+    const double *SY = SYg, *YBY = YBYg;
+    long long ls = kmax;
+    if (mats) {
+        double *S1 = rdiag + k, *S2 = S1 + (size_t)k * k;
+        for (int q = lane; q < k * k; q += 32) {
+            const int i = q / k, j = q - i * k;
+            S1[q] = __ldg(SYg + (long long)i * kmax + j);
+            S2[q] = __ldg(YBYg + (long long)i * kmax + j);
+        }
+        SY = S1;
+        YBY = S2;
+        ls = k;
+    }
+    for (int i = lane; i < k; i += 32) rdiag[i] = 1.0 / __ldg(SYg + (long long)i * kmax + i);
+    __syncwarp();
+    double x[NJ], cv[NJ], acc[NJ];
+#pragma unroll
+    for (int t = 0; t < NJ; ++t) {
+        const int j = lane + 32 * t;
+        x[t] = j < k ? __ldg(T + (long long)j * p + c) : 0.0;
+        cv[t] = 0.0;
+        acc[t] = 0.0;
+    }
+    // R cv = T_top (back substitution), R_ij = s_i^T y_j upper: cv_i final at step i
+    for (int i = k - 1; i >= 0; --i) {
+        const int ti = i >> 5, li = i & 31;
+        const double v = __shfl_sync(0xffffffffu, pick_nj<NJ>(x, ti) * rdiag[i], li);
+#pragma unroll
+        for (int t = 0; t < NJ; ++t) {
+            const int j = lane + 32 * t;
+            if (t == ti && lane == li) cv[t] = v;
+            if (j < i) x[t] = fma(-SY[j * ls + i], v, x[t]);
+        }
+    }
+    // acc = Y^T B0 Y cv (column by column over the broadcast cv_i)
+    for (int i = 0; i < k; ++i) {
+        const double v = __shfl_sync(0xffffffffu, pick_nj<NJ>(cv, i >> 5), i & 31);
+#pragma unroll
+        for (int t = 0; t < NJ; ++t) {
+            const int j = lane + 32 * t;
+            if (j < k) acc[t] = fma(YBY[j * ls + i], v, acc[t]);
+        }
+    }
+    // d = D cv + gamma (Y^T B0 Y cv - t2), then R^T top = d (forward substitution)
+#pragma unroll
+    for (int t = 0; t < NJ; ++t) {
+        const int j = lane + 32 * t;
+        x[t] = j < k ? SY[j * ls + j] * cv[t] + gamma * acc[t] - gamma * __ldg(T + (long long)(k + j) * p + c) : 0.0;
+    }
+    double top[NJ];
+#pragma unroll
+    for (int t = 0; t < NJ; ++t) top[t] = 0.0;
+    for (int i = 0; i < k; ++i) {
+        const int ti = i >> 5, li = i & 31;
+        const double v = __shfl_sync(0xffffffffu, pick_nj<NJ>(x, ti) * rdiag[i], li);
+#pragma unroll
+        for (int t = 0; t < NJ; ++t) {
+            const int j = lane + 32 * t;
+            if (t == ti && lane == li) top[t] = v;
+            if (j > i && j < k) x[t] = fma(-SY[i * ls + j], v, x[t]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NJ; ++t) {
+        const int j = lane + 32 * t;
+        if (j >= k) continue;
+        const double bot = -gamma * cv[t];
+        if (coef) {
+            coef[(long long)c * 2 * k + j] = (float)top[t];
+            coef[(long long)c * 2 * k + k + j] = (float)bot;
+        }
+        if (coefd) {
+            coefd[(long long)c * 2 * k + j] = top[t];
+            coefd[(long long)c * 2 * k + k + j] = bot;
+        }
+    }
+}
+
 // out[i][j] = sum_l A(i, l) B(l, j), i < M, j < N, l < K, with A(i, l) =
 // A[i ar + l ac] and B(l, j) = B[l br + j bc] (any transposition by the
 // strides), FP64 accumulation in l order; one thread per output element,
@@ -1068,10 +1173,11 @@ int launch_middle(gbfwi_bfgs *h, const double *T, int q, double gamma, float *co
     const int k = h->k;
     const int mats = middle_smem_bytes(k, true) <= 200 * 1024;
     const size_t bytes = middle_smem_bytes(k, mats);
+    auto kern = k <= 32 ? middle_col_kernel<1> : k <= 64 ? middle_col_kernel<2> : k <= 128 ? middle_col_kernel<4>
+                                                                                       : middle_kernel;
     if (bytes > 48 * 1024)
-        GB_CUDA(cudaFuncSetAttribute(middle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    middle_kernel<<<q, 32, bytes, s>>>(T, h->dSY.as<double>(), h->dYBY.as<double>(), k, h->kmax, q, gamma, mats,
-                                       coef, coefd);
+        GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    kern<<<q, 32, bytes, s>>>(T, h->dSY.as<double>(), h->dYBY.as<double>(), k, h->kmax, q, gamma, mats, coef, coefd);
     GB_LAUNCHED();
     return GBFWI_OK;
 }
